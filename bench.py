@@ -1,0 +1,320 @@
+"""Benchmark of the FK-convolution fit step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P] [--impl ours|reference]
+
+A step is one pass of the whole hot path over the global-shaped fit set
+(40 synthetic datasets, 12 DIS + 28 hadronic, ~4500 data points, R = 100
+replicas on a shared 50-point x grid): forward convolution of every table,
+FP64 chi^2 with its gradient, adjoint of every table into dchi2/dF.  The
+metric is datapoint*replicas per second (sum of ndata * R over the step,
+divided by the step time).  Tables are device resident; the timed region
+replays the step's CUDA graphs.  Under torchrun each rank runs its own copy
+of the workload (weak scaling, no collective on the data path); rank 0
+prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "FK conv datapoint·replicas/s"
+UNIT = "datapoint·replicas/s"
+REPLICAS = 100
+SEED = 10547 + 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        return m, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+            "sm_max_mhz": 2032.0}, "fallback"
+
+
+def dist_init(n):
+    import torch
+    import torch.distributed as dist
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    rank = int(os.environ["RANK"])
+    world = int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, world, dist
+
+
+def max_over_ranks(dist, x):
+    import torch
+    if dist is None:
+        return x
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload():
+    from paper_1909_10547_b300 import workloads as W
+    g = W.config3(R=REPLICAS, seed=SEED)
+    return g
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+        return False
+
+    def summary(self):
+        if self.p is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(g, replicas):
+    """The FP64 oracle (as it stands) on a bounded sample: the same fit step
+    for the first `replicas` replicas.  Returns (dp*rep/s, threads, seconds)."""
+    import oracle
+    from paper_1909_10547_b300 import workloads as W
+    F = g.F[:replicas]
+    # set-up outside the timed region: covariance factors and pseudo-data
+    o_true = [oracle.conv(t, g.F_true)[0][0] for t in g.tables]
+    cov = W.covariance(o_true, SEED)
+    D = W.pseudo_data(o_true, SEED)
+    Ls = [oracle.cholesky(b) for b in cov.blocks]
+    t0 = time.perf_counter()
+    for t, L, d in zip(g.tables, Ls, D):
+        O, _ = oracle.conv(t, F)
+        _, gO = oracle.chi2(L, O, d)
+        oracle.conv_grad(t, F, gO)
+    dt = time.perf_counter() - t0
+    ntot = sum(t.ndata for t in g.tables)
+    return ntot * replicas / dt, oracle.threads(), dt
+
+
+def run_reference(args, rank, world, dist):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    g = workload()
+    per_step = max(1, min(8, int(150.0 / (0.5 * (args.steps + args.warmup)))))
+    import oracle
+    from paper_1909_10547_b300 import workloads as W
+    o_true = [oracle.conv(t, g.F_true)[0][0] for t in g.tables]
+    cov = W.covariance(o_true, SEED)
+    D = W.pseudo_data(o_true, SEED)
+    Ls = [oracle.cholesky(b) for b in cov.blocks]
+    F = g.F[:per_step]
+
+    def step():
+        for t, L, d in zip(g.tables, Ls, D):
+            O, _ = oracle.conv(t, F)
+            _, gO = oracle.chi2(L, O, d)
+            oracle.conv_grad(t, F, gO)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    ntot = sum(t.ndata for t in g.tables)
+    v = ntot * per_step / dt
+    sample = f"{per_step} of {REPLICAS} replicas per step, all 40 tables, FP64"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_dict(g, "fp64"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(g, prec):
+    ntot = sum(t.ndata for t in g.tables)
+    return {"workload": "global-shaped chi2 fit step (forward + FP64 chi2 + adjoint): 40 datasets "
+                        "(12 DIS, 28 hadronic), nx 20..50 on a 50-point grid, 20..120 channels",
+            "ndata_total": ntot, "replicas": REPLICAS, "tables": len(g.tables), "prec": prec,
+            "l2": "inputs larger than L2 (resident FK tables ~1.4 GB FP32)",
+            "graphs": True, "parallelism": "replicas only (one independent copy per rank)"}
+
+
+def main():
+    args = parse()
+    import torch
+    rank, world, dist = dist_init(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    from paper_1909_10547_b300.fitstep import GlobalFit
+
+    dev = torch.cuda.current_device()
+    g = workload()
+    # pseudo-data: D = O(f_true) + correlated noise, O(f_true) from the FP64 path
+    tabs64 = [fk.Table.from_workload(t, ("fp64",)) for t in g.tables]
+    Ft = torch.tensor(g.F_true, device="cuda")
+    o_true = [fk.conv(t, Ft, "fp64")[0].cpu().numpy() for t in tabs64]
+    del tabs64
+    cov = W.covariance(o_true, SEED)
+    D = np.concatenate(W.pseudo_data(o_true, SEED))
+    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec)
+    fit.capture()
+    launches = fit.launches_per_step()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        fit.step()
+    torch.cuda.synchronize()
+    names = list(fit.graphs)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    # the timed region is also the profiler range (ncu --profile-from-start off)
+    torch.cuda.cudart().cudaProfilerStart()
+    with Clocks(dev) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            for i, n in enumerate(names):
+                fit.graphs[n].replay()
+                ev[k][i + 1].record(stream)
+        torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    if dist is not None:
+        dist.barrier()
+    seg = {n: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+           for i, n in enumerate(names)}
+    ms = sum(ev[k][0].elapsed_time(ev[k][-1]) for k in range(args.steps)) / args.steps
+    ms = max_over_ranks(dist, ms)
+
+    # end to end: pinned host F in, chi2 and gF out, through the same calls
+    F_host = torch.tensor(g.F, dtype=fit.io).pin_memory()
+    chi2_host = torch.empty(fit.R, dtype=torch.float64).pin_memory()
+    gF_host = torch.empty(fit.gF.shape, dtype=fit.io).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        fit.F.copy_(F_host, non_blocking=True)
+        fit.step()
+        chi2_host.copy_(fit.chi2, non_blocking=True)
+        gF_host.copy_(fit.gF, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fit.F.copy_(F_host, non_blocking=True)
+        fit.step()
+        chi2_host.copy_(fit.chi2, non_blocking=True)
+        gF_host.copy_(fit.gF, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
+
+    units = fit.ntot * fit.R
+    value = units * world / (ms * 1e-3)
+    pk, pk_src = peaks()
+    dom = max(seg, key=seg.get)
+    if args.prec in ("bf16", "bf16x3", "tf32"):
+        bound, peak, unit = "tensor", pk["bf16_tflops_sustained"], "TFLOP/s"
+        if args.prec == "tf32":
+            peak = peak / 2.0
+    elif args.prec == "fp32":
+        # FP32 CUDA cores: 148 SMs x 128 lanes x 2 flop x max SM clock
+        bound, peak, unit = "alu", 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12, "TFLOP/s"
+    else:
+        bound, peak, unit = "alu", 1.25, "TFLOP/s"
+    achieved = fit.flops[dom] / (seg[dom] * 1e-3) / 1e12
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "kernel": f"{dom} phase",
+            "peak_source": pk_src, "phase_ms": seg}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16",
+                                           "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
+            "data": "synthetic", "config": config_dict(g, args.prec), "roofline": roof,
+            "e2e": {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": F_host.numel() * F_host.element_size(),
+                    "d2h_bytes_per_step": chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size()},
+            "gpu_launches": launches * args.steps, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, dt = cpu_baseline(g, 32)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"32 of {REPLICAS} replicas, whole fit step, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * fk.h -- C ABI of the B300 FK-table convolution library (libfk.so).
+ *
+ * The library evaluates the observables of a PDF fit from precomputed Fast
+ * Kernel (FK) tables, as in Sec. 3 of arXiv:1909.10547 ("Towards hardware
+ * acceleration for parton densities estimation"):
+ *
+ *   hadronic (Eq. 1):  O[r][d] = sum_c sum_i sum_j FK[d][c][i][j] f^r_{a_c}(x_i) f^r_{b_c}(x_j)
+ *   DIS:               O[r][d] = sum_k sum_i     FK[d][k][i]    f^r_{a_k}(x_i)
+ *
+ * for R PDF replicas r at once (Sec. 3: fitting all replicas simultaneously on
+ * the accelerator), together with the gradient of the observables with
+ * respect to the PDF (the custom operator's gradient, Sec. 3 and Table 1), the
+ * chi^2 of the fit with an FP64 Cholesky-factorised covariance, and a
+ * continuously batched serving loop over device-resident tables.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status (FK_OK = 0 or an FK_E* code) and
+ *    never throws.  fk_last_error_message() gives a human-readable detail for
+ *    the calling thread's last failure.
+ *  - Flavours are the 14 evolution-basis flavours, indexed 0..13.
+ *  - PDF replicas F are laid out [R][14][nx_grid], row-major, where nx_grid is
+ *    the size of the x grid the PDFs are sampled on.  A table is defined on nx
+ *    of those points; xmap[i] (strictly increasing is not required, but the
+ *    entries must be distinct) gives the grid index of the table's x_i.
+ *  - Observables O are laid out [R][ndata]; gradients gF like F.
+ *  - "Device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *    passes; the library owns tables, covariances and servers, which live until
+ *    the matching *_destroy call.
+ *  - Asynchronous calls (fk_*_conv, fk_conv_backward, fk_chi2) enqueue work on
+ *    `stream` (a cudaStream_t; NULL means the legacy default stream) and return
+ *    before it completes.  Input buffers must stay valid, and outputs must not
+ *    be read, until the stream has reached that point.  Temporary device
+ *    memory comes from CUDA's stream-ordered allocator on the same stream.
+ *  - Argument errors are detected on the host before anything is enqueued:
+ *    such a call returns FK_EINVAL and enqueues nothing.
+ */
+#ifndef FK_H
+#define FK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fk_table fk_table;
+typedef struct fk_cov fk_cov;
+typedef struct fk_server fk_server;
+typedef void *fk_stream; /* cudaStream_t */
+
+/* Status codes. */
+enum {
+    FK_OK = 0,
+    FK_EINVAL = 1,      /* bad argument (shape, pointer, precision, index) */
+    FK_ENOMEM = 2,      /* device or host allocation failed */
+    FK_EBUDGET = 3,     /* request can never fit the server's memory budget */
+    FK_EPENDING = 4,    /* served request not finished yet */
+    FK_ETIMEDOUT = 5,   /* a bounded wait ran out */
+    FK_ECUDA = 6,       /* a CUDA runtime call or kernel launch failed */
+    FK_ENOTFOUND = 7,   /* unknown ticket or table id */
+    FK_EUNSUPPORTED = 8 /* precision not stored in this table, or not offered */
+};
+
+/* Arithmetic modes.  FP64 and FP32 read and write buffers of that type.  The
+ * reduced modes read FP32 F and write FP32 O; the table's stored copy and the
+ * packed PDF operand are rounded to the mode's type, products go through the
+ * tensor cores and accumulate in FP32.  BF16X3 splits each operand into
+ * hi = bf16(v), lo = bf16(v - hi) and sums hi*hi + hi*lo + lo*hi. */
+enum {
+    FK_FP64 = 0,
+    FK_FP32 = 1,
+    FK_BF16 = 2,
+    FK_BF16X3 = 3,
+    FK_TF32 = 4
+};
+#define FK_PREC_BIT(p) (1u << (p))
+
+/* Table kinds reported by fk_table_info. */
+enum { FK_KIND_DIS = 0, FK_KIND_HAD = 1 };
+
+/* ---------------------------------------------------------------- errors */
+
+/* Static description of a status code. */
+const char *fk_strerror(int status);
+/* Detail of the calling thread's most recent failure ("" if none). */
+const char *fk_last_error_message(void);
+/* Library ABI version (major * 100 + minor). */
+int fk_version(void);
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices); for accounting in benchmarks. */
+uint64_t fk_kernel_launches(void);
+
+/* ---------------------------------------------------------------- tables */
+
+/*
+ * DIS FK table: fk is HOST memory, [ndata][nflav][nx] FP64, holding the
+ * slices of the nflav active flavours flav[0..nflav) (each in 0..13,
+ * distinct).  xmap (host, [nx], may be NULL for the identity with
+ * nx_grid == nx) maps x_i to the PDF grid of size nx_grid.  prec_mask is an OR
+ * of FK_PREC_BIT(p) for each precision to keep on the device.  The data are
+ * copied; the caller may free its arrays on return.
+ * Errors: FK_EINVAL (sizes <= 0, nx_grid < nx, flavour or xmap out of range,
+ * empty mask), FK_ENOMEM, FK_ECUDA.
+ */
+int fk_table_create_dis(const double *fk, int ndata, const int *flav, int nflav, int nx,
+                        const int *xmap, int nx_grid, unsigned prec_mask, fk_table **out);
+
+/*
+ * Hadronic FK table (Eq. 1): fk is HOST memory, [ndata][nc][nx][nx] FP64, one
+ * nx*nx block per active channel c coupling flavour ca[c] at x_i (first x
+ * index) with flavour cb[c] at x_j (second x index).  Channels are ordered
+ * pairs and must be distinct; (a, a) is allowed.  Other arguments as for
+ * fk_table_create_dis.
+ */
+int fk_table_create_had(const double *fk, int ndata, const int *ca, const int *cb, int nc,
+                        int nx, const int *xmap, int nx_grid, unsigned prec_mask,
+                        fk_table **out);
+
+/* Frees the table's device memory.  NULL is accepted. */
+int fk_table_destroy(fk_table *t);
+
+/* Shape and resident size of a table.  Any output pointer may be NULL. */
+int fk_table_info(const fk_table *t, int *kind, int *ndata, int *nchannels, int *nx,
+                  int *nx_grid, unsigned *prec_mask, size_t *device_bytes);
+
+/* ---------------------------------------------------------- convolution */
+
+/*
+ * DIS observables of table t (kind DIS) for R >= 1 replicas.
+ * F: DEVICE [R][14][nx_grid] (double for FK_FP64, float otherwise).
+ * O: DEVICE, same type, replica r's ndata values at O + r * ldo (ldo = 0
+ *    means ldo = ndata, i.e. a dense [R][ndata] array); overwritten.  A
+ *    larger ldo lets several tables write into one [R][sum ndata] vector.
+ * Errors: FK_EINVAL (wrong kind, R < 1, NULL pointer, 0 < ldo < ndata),
+ * FK_EUNSUPPORTED (precision not in the table's mask), FK_ENOMEM, FK_ECUDA.
+ */
+int fk_dis_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
+                fk_stream stream);
+
+/* Hadronic observables (Eq. 1) of table t (kind HAD); arguments as above. */
+int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
+                fk_stream stream);
+
+/*
+ * Adjoint of the convolution (the gradient of Sec. 3 / Table 1):
+ *   gF[r][a][xmap[i]] (+)= sum_d gO[r][d] * dO[r][d] / df^r_a(x_i)
+ * for either table kind.  F: DEVICE [R][14][nx_grid]; gO: DEVICE, replica
+ * r's ndata values at gO + r * ldgo (ldgo = 0 means ndata); gF: DEVICE
+ * [R][14][nx_grid]; all of the mode's I/O type (double for FK_FP64, float
+ * otherwise).  accumulate = 0 overwrites all of gF (grid points the table does
+ * not use are set to 0); accumulate = 1 adds into gF, so the gradients of
+ * several tables sharing one grid can be summed in call order.  F is not read
+ * for DIS tables (may be NULL).  Reduced modes compute in FP32 on the CUDA
+ * cores and need the table's FP32 copy (FK_EUNSUPPORTED otherwise).
+ */
+int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
+                     void *gF, int accumulate, int prec, fk_stream stream);
+
+/* ---------------------------------------------------------------- chi^2 */
+
+/*
+ * Block-diagonal experimental covariance, one dense SPD block per dataset.
+ * C_blocks: HOST FP64, the blocks one after another, each row-major
+ * [n_k][n_k]; block_sizes: HOST [nblocks].  The blocks are copied to the
+ * device and factorised there in FP64 (C_k = L_k L_k^T), and each L_k is
+ * inverted by triangular solves against the identity.  The call synchronises
+ * with the device.  Errors: FK_EINVAL (sizes, or a block that is not
+ * positive definite: a non-positive pivot), FK_ENOMEM, FK_ECUDA.
+ */
+int fk_cov_create(const double *C_blocks, const int *block_sizes, int nblocks, fk_cov **out);
+int fk_cov_destroy(fk_cov *cov);
+/* Total dimension sum_k n_k (0 for NULL). */
+int fk_cov_size(const fk_cov *cov);
+
+/*
+ * chi^2 per replica: chi2[r] = (O_r - D)^T C^{-1} (O_r - D), evaluated in
+ * FP64 as |L^{-1}(O_r - D)|^2 blockwise.  If gO is not NULL it receives
+ * d chi2[r] / d O_r = 2 C^{-1} (O_r - D).
+ * O: DEVICE [R][n] and gO: DEVICE [R][n] or NULL, both double if io_prec is
+ * FK_FP64 and float for any other mode (so the observables and gradient of a
+ * reduced-precision fit need no conversion; the arithmetic is FP64 either
+ * way).  D: DEVICE [n] double; chi2: DEVICE [R] double (n = fk_cov_size).
+ * Errors: FK_EINVAL, FK_ENOMEM, FK_ECUDA.
+ */
+int fk_chi2(const fk_cov *cov, const void *O, const double *D, int R, double *chi2, void *gO,
+            int io_prec, fk_stream stream);
+
+/* -------------------------------------------------------------- serving */
+
+/*
+ * A server owns a scheduler thread and its own CUDA streams.  Tables added to
+ * it stay resident on the device.  Requests (table, PDF replicas, precision)
+ * are admitted while the device memory they need fits in hbm_budget_bytes
+ * (counting the resident tables) and fewer than max_inflight are running;
+ * requests on the same table and precision that are waiting together are
+ * coalesced along the replica axis into one launch.  Each result equals the
+ * same request run alone (bit for bit in FK_FP64 and FK_FP32 modes).
+ */
+int fk_serve_create(size_t hbm_budget_bytes, int max_inflight, fk_server **out);
+/* Registers table t (the server does not take ownership; keep t alive until
+ * fk_serve_destroy).  FK_EBUDGET if the table alone exceeds the budget. */
+int fk_serve_add_table(fk_server *s, fk_table *t, int *table_id);
+/*
+ * Queues a request.  F_host: HOST [R][14][nx_grid] of the mode's I/O type; it
+ * is copied before the call returns.  *ticket identifies the request.
+ * FK_EBUDGET if the request could never fit the budget, FK_ENOTFOUND for an
+ * unknown table id, FK_EUNSUPPORTED for a precision the table lacks.
+ */
+int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int prec,
+                    uint64_t *ticket);
+/*
+ * Non-blocking.  If the request is done, copies its O ([R][ndata], I/O type)
+ * to O_host, sets *done = 1, forgets the ticket and returns the request's
+ * status; otherwise sets *done = 0 and returns FK_EPENDING.
+ */
+int fk_serve_poll(fk_server *s, uint64_t ticket, void *O_host, int *done);
+/* As fk_serve_poll, but waits up to timeout_ms (FK_ETIMEDOUT after that). */
+int fk_serve_wait(fk_server *s, uint64_t ticket, void *O_host, int timeout_ms);
+/*
+ * Counters since creation: completed requests, sum of ndata*R over them,
+ * device launches, peak bytes in use (tables + in-flight requests), queue
+ * depth now.  Any pointer may be NULL.
+ */
+int fk_serve_stats(const fk_server *s, uint64_t *completed, uint64_t *datapoint_replicas,
+                   uint64_t *launches, size_t *peak_bytes, int *queued);
+/* Stops the scheduler after the requests in flight finish; frees requests. */
+int fk_serve_destroy(fk_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FK_H */

@@ -1,0 +1,227 @@
+"""B300-native FK-table convolution (arXiv:1909.10547, Sec. 3).
+
+A thin binding over libfk.so: every function marshals torch tensors (device
+memory and the current CUDA stream) into the C ABI of include/fk.h and raises
+FKError on a non-zero status.  All arithmetic runs in the library's CUDA
+kernels; there is no CPU fallback.
+
+    t  = Table.had(fk, ca, cb, xmap=None, nx_grid=None, precs=("fp64", "fp32"))
+    O  = conv(t, F, "fp32")                 # F [R][14][nx_grid] on cuda
+    gF = conv_backward(t, F, gO, "fp32")
+    cov = Cov(blocks);  chi2_r, gO = chi2(cov, O, D)
+    O  = FKConv.apply(F, t, "fp32")         # autograd
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FKError, PRECS
+
+__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "Cov", "chi2", "FKConv",
+           "FKError", "PRECS", "lib_path"]
+
+NFL = 14
+
+
+def lib_path() -> str:
+    return _lib.path()
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return x
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _prec(p):
+    if isinstance(p, int):
+        return p
+    return PRECS[p]
+
+
+def _io_dtype(prec):
+    return torch.float64 if _prec(prec) == _lib.FK_FP64 else torch.float32
+
+
+def _mask(precs):
+    m = 0
+    for p in precs:
+        m |= 1 << _prec(p)
+    return m
+
+
+class Table:
+    """A device-resident FK table (owned by the library)."""
+
+    def __init__(self, handle, kind, ndata, nch, nx, nxg):
+        self._h = handle
+        self.kind, self.ndata, self.nch, self.nx, self.nxg = kind, ndata, nch, nx, nxg
+
+    @classmethod
+    def dis(cls, fk_compact, flav, xmap=None, nx_grid=None, precs=("fp64", "fp32")):
+        """fk_compact [ndata][nflav][nx] (host, FP64) for active flavours flav."""
+        fk = np.ascontiguousarray(fk_compact, dtype=np.float64)
+        nd, nfl, nx = fk.shape
+        flav = np.ascontiguousarray(flav, dtype=np.int32)
+        xm = None if xmap is None else np.ascontiguousarray(xmap, dtype=np.int32)
+        nxg = nx if nx_grid is None else int(nx_grid)
+        h = ctypes.c_void_p()
+        _lib.call("fk_table_create_dis", _p(fk), nd, _p(flav), nfl, nx, _p(xm), nxg, _mask(precs),
+                  ctypes.byref(h))
+        return cls(h, 0, nd, nfl, nx, nxg)
+
+    @classmethod
+    def had(cls, fk, ca, cb, xmap=None, nx_grid=None, precs=("fp64", "fp32")):
+        """fk [ndata][nc][nx][nx] (host, FP64); channel c = (ca[c], cb[c])."""
+        fk = np.ascontiguousarray(fk, dtype=np.float64)
+        nd, nc, nx, _ = fk.shape
+        ca = np.ascontiguousarray(ca, dtype=np.int32)
+        cb = np.ascontiguousarray(cb, dtype=np.int32)
+        xm = None if xmap is None else np.ascontiguousarray(xmap, dtype=np.int32)
+        nxg = nx if nx_grid is None else int(nx_grid)
+        h = ctypes.c_void_p()
+        _lib.call("fk_table_create_had", _p(fk), nd, _p(ca), _p(cb), nc, nx, _p(xm), nxg,
+                  _mask(precs), ctypes.byref(h))
+        return cls(h, 1, nd, nc, nx, nxg)
+
+    @classmethod
+    def from_workload(cls, t, precs=("fp64", "fp32")):
+        """Builds a device table from a workloads.DisTable / HadTable."""
+        if hasattr(t, "ca"):
+            return cls.had(t.fk, t.ca, t.cb, t.xmap, t.nxg, precs)
+        return cls.dis(t.compact(), t.flav, t.xmap, t.nxg, precs)
+
+    def device_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _lib.call("fk_table_info", self._h, None, None, None, None, None, None, ctypes.byref(n))
+        return n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.load().fk_table_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_f(t, F, prec):
+    dt = _io_dtype(prec)
+    if not (F.is_cuda and F.dtype == dt and F.is_contiguous() and F.dim() == 3
+            and F.shape[1] == NFL and F.shape[2] == t.nxg):
+        raise ValueError(f"F must be a contiguous cuda {dt} tensor [R][14][{t.nxg}]")
+
+
+def conv(t: Table, F: torch.Tensor, prec="fp32", out: torch.Tensor = None) -> torch.Tensor:
+    """Observables O [R][ndata] of table t for replicas F [R][14][nx_grid].
+
+    out may be a column slice out[:, off:off+ndata] of a wider [R][n] tensor
+    (unit stride along data points): the row stride is passed as ldo."""
+    _check_f(t, F, prec)
+    R = F.shape[0]
+    O = out if out is not None else torch.empty((R, t.ndata), dtype=F.dtype, device=F.device)
+    if O.shape != (R, t.ndata) or O.stride(1) != 1 or O.dtype != F.dtype:
+        raise ValueError("out must be [R][ndata] with unit column stride and F's dtype")
+    name = "fk_had_conv" if t.kind == 1 else "fk_dis_conv"
+    _lib.call(name, t.handle, _p(F), R, _p(O), O.stride(0), _prec(prec), _stream())
+    return O
+
+
+def dis_conv(t, F, prec="fp32", out=None):
+    assert t.kind == 0
+    return conv(t, F, prec, out)
+
+
+def had_conv(t, F, prec="fp32", out=None):
+    assert t.kind == 1
+    return conv(t, F, prec, out)
+
+
+def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False):
+    """gF [R][14][nx_grid] (+)= sum_d gO[r][d] dO[r][d]/dF[r]."""
+    dt = _io_dtype(prec)
+    R = gO.shape[0]
+    if gF is None:
+        gF = torch.empty((R, NFL, t.nxg), dtype=dt, device=gO.device)
+        accumulate = False
+    if gO.stride(1) != 1:
+        raise ValueError("gO needs unit stride along data points")
+    _lib.call("fk_conv_backward", t.handle, _p(F), _p(gO), gO.stride(0), R, _p(gF),
+              int(bool(accumulate)), _prec(prec), _stream())
+    return gF
+
+
+class Cov:
+    """Block-diagonal covariance factorised on the device (FP64)."""
+
+    def __init__(self, blocks):
+        sizes = np.array([b.shape[0] for b in blocks], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64).ravel() for b in blocks]))
+        h = ctypes.c_void_p()
+        _lib.call("fk_cov_create", _p(flat), _p(sizes), len(blocks), ctypes.byref(h))
+        self._h = h
+        self.n = int(sizes.sum())
+        self.sizes = sizes
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.load().fk_cov_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def chi2(cov: Cov, O: torch.Tensor, D: torch.Tensor, grad=True, out=None, gO=None):
+    """chi2 [R] (FP64) and, if grad, dchi2/dO [R][n] in O's dtype.  O may be
+    FP64 or FP32; the arithmetic is FP64 on the device either way."""
+    R = O.shape[0]
+    if not O.is_contiguous() or O.shape[1] != cov.n:
+        raise ValueError(f"O must be contiguous [R][{cov.n}]")
+    io = _lib.FK_FP64 if O.dtype == torch.float64 else _lib.FK_FP32
+    c = out if out is not None else torch.empty(R, dtype=torch.float64, device=O.device)
+    g = None
+    if grad:
+        g = gO if gO is not None else torch.empty_like(O)
+    _lib.call("fk_chi2", cov.handle, _p(O), _p(D), R, _p(c), _p(g), io, _stream())
+    return c, g
+
+
+class FKConv(torch.autograd.Function):
+    """O = conv(t, F); backward gives dL/dF through the library's adjoint."""
+
+    @staticmethod
+    def forward(ctx, F, t, prec="fp32"):
+        ctx.t, ctx.prec = t, prec
+        ctx.save_for_backward(F)
+        return conv(t, F.contiguous(), prec)
+
+    @staticmethod
+    def backward(ctx, gO):
+        (F,) = ctx.saved_tensors
+        gF = conv_backward(ctx.t, F.contiguous(), gO.contiguous(), ctx.prec)
+        return gF, None, None

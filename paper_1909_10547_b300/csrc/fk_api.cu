@@ -1,0 +1,269 @@
+// C ABI of the FK convolution library: errors, tables, convolution dispatch.
+#include "fk_internal.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <set>
+#include <utility>
+
+namespace fk {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+int fail(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? FK_ENOMEM : FK_ECUDA;
+}
+
+namespace {
+
+constexpr unsigned ALL_PRECS = FK_PREC_BIT(FK_FP64) | FK_PREC_BIT(FK_FP32) | FK_PREC_BIT(FK_BF16) |
+                               FK_PREC_BIT(FK_BF16X3) | FK_PREC_BIT(FK_TF32);
+constexpr unsigned TC_PRECS = FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3) | FK_PREC_BIT(FK_TF32);
+
+void keep_pool() {
+    // Keep freed stream-ordered scratch in the device pool instead of
+    // returning it to the driver after every synchronisation.
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = true;
+}
+
+void table_free(fk_table *t) {
+    if (!t) return;
+    cudaFree(t->d_ca);
+    cudaFree(t->d_cb);
+    cudaFree(t->d_xmap);
+    cudaFree(t->d_xinv);
+    cudaFree(t->fk64);
+    cudaFree(t->fk32);
+    tc_free(t);
+    delete t;
+}
+
+template <typename T>
+int upload(T **d, const std::vector<T> &h, size_t *bytes) {
+    if (h.empty()) return FK_OK;
+    if (cudaMalloc(d, sizeof(T) * h.size())) return fail(FK_ENOMEM, "table index arrays");
+    FK_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    *bytes += sizeof(T) * h.size();
+    return FK_OK;
+}
+
+int table_create(int kind, const double *fk, int ndata, const int *ca, const int *cb, int nch,
+                 int nx, const int *xmap, int nxg, unsigned mask, fk_table **out) {
+    if (!out) return fail(FK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!fk || !ca || (kind == FK_KIND_HAD && !cb)) return fail(FK_EINVAL, "null table or channel array");
+    if (ndata < 1) return fail(FK_EINVAL, "ndata < 1");
+    if (nx < 1 || nx > MAX_NX) return fail(FK_EINVAL, "nx must be in 1..64");
+    if (nxg < nx || nxg > MAX_NXG) return fail(FK_EINVAL, "nx_grid must be in nx..64");
+    if (!mask || (mask & ~ALL_PRECS)) return fail(FK_EINVAL, "bad precision mask");
+    const int maxch = kind == FK_KIND_HAD ? MAX_CH : NFL;
+    if (nch < 1 || nch > maxch) return fail(FK_EINVAL, "channel count out of range");
+    std::set<std::pair<int, int>> seen;
+    for (int c = 0; c < nch; ++c) {
+        const int a = ca[c], b = kind == FK_KIND_HAD ? cb[c] : 0;
+        if (a < 0 || a >= NFL || b < 0 || b >= NFL) return fail(FK_EINVAL, "flavour index out of 0..13");
+        if (!seen.insert({a, b}).second) return fail(FK_EINVAL, "duplicate channel or flavour");
+    }
+    std::vector<int> xm(nx), xinv(nxg, -1);
+    for (int i = 0; i < nx; ++i) {
+        xm[i] = xmap ? xmap[i] : i;
+        if (xm[i] < 0 || xm[i] >= nxg) return fail(FK_EINVAL, "xmap entry out of range");
+        if (xinv[xm[i]] >= 0) return fail(FK_EINVAL, "xmap entries must be distinct");
+        xinv[xm[i]] = i;
+    }
+    if (kind == FK_KIND_DIS && (mask & TC_PRECS))
+        return fail(FK_EUNSUPPORTED, "DIS tables offer FP64 and FP32 only");
+
+    keep_pool();
+    fk_table *t = new fk_table();
+    t->kind = kind;
+    t->ndata = ndata;
+    t->nch = nch;
+    t->nx = nx;
+    t->nxg = nxg;
+    t->E = kind == FK_KIND_HAD ? (long long)nch * nx * nx : (long long)nch * nx;
+    t->ldE = (t->E + 31) / 32 * 32;
+    t->mask = mask;
+    cudaGetDevice(&t->device);
+    t->ca.assign(ca, ca + nch);
+    if (kind == FK_KIND_HAD) t->cb.assign(cb, cb + nch);
+    t->xmap = xm;
+    int rc = FK_OK;
+    if ((rc = upload(&t->d_ca, t->ca, &t->bytes)) || (rc = upload(&t->d_cb, t->cb, &t->bytes)) ||
+        (rc = upload(&t->d_xmap, t->xmap, &t->bytes)) || (rc = upload(&t->d_xinv, xinv, &t->bytes))) {
+        table_free(t);
+        return rc;
+    }
+    const size_t rowsz = (size_t)t->ldE * ndata;
+    const bool need64 = mask & FK_PREC_BIT(FK_FP64);
+    const bool need32 = mask & FK_PREC_BIT(FK_FP32);
+    if ((need64 && cudaMalloc(&t->fk64, sizeof(double) * rowsz)) ||
+        (need32 && cudaMalloc(&t->fk32, sizeof(float) * rowsz))) {
+        table_free(t);
+        return fail(FK_ENOMEM, "table storage");
+    }
+    t->bytes += (need64 ? sizeof(double) * rowsz : 0) + (need32 ? sizeof(float) * rowsz : 0);
+    if (need64 || need32) {
+        // stage the host rows through a bounded device buffer
+        const long long rows_per = std::max(1LL, (64LL << 20) / (t->E * 8));
+        double *stage = nullptr;
+        cudaStream_t st = nullptr;
+        if (cudaMalloc(&stage, sizeof(double) * t->E * std::min<long long>(rows_per, ndata)) ||
+            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) {
+            cudaFree(stage);
+            table_free(t);
+            return fail(FK_ENOMEM, "table staging buffer");
+        }
+        for (long long d0 = 0; d0 < ndata && rc == FK_OK; d0 += rows_per) {
+            const long long nr = std::min<long long>(rows_per, ndata - d0);
+            cudaError_t e = cudaMemcpyAsync(stage, fk + d0 * t->E, sizeof(double) * nr * t->E,
+                                            cudaMemcpyHostToDevice, st);
+            if (e) {
+                rc = cuda_fail(e, "table upload");
+                break;
+            }
+            rc = convert_rows(stage, nr, t->E, t->ldE, t->fk64 ? t->fk64 + d0 * t->ldE : nullptr,
+                              t->fk32 ? t->fk32 + d0 * t->ldE : nullptr, st);
+            if (!rc) {
+                e = cudaStreamSynchronize(st);
+                if (e) rc = cuda_fail(e, "table conversion");
+            }
+        }
+        cudaStreamDestroy(st);
+        cudaFree(stage);
+        if (rc) {
+            table_free(t);
+            return rc;
+        }
+    }
+    if (mask & TC_PRECS) {
+        rc = tc_build(t, fk);
+        if (rc) {
+            table_free(t);
+            return rc;
+        }
+    }
+    *out = t;
+    return FK_OK;
+}
+
+int check_conv(const fk_table *t, int kind, const void *F, int R, const void *O, int ldo, int prec) {
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (t->kind != kind) return fail(FK_EINVAL, "wrong table kind for this call");
+    if (!F || !O) return fail(FK_EINVAL, "null F or O");
+    if (R < 1) return fail(FK_EINVAL, "R < 1");
+    if (ldo < 0 || (ldo > 0 && ldo < t->ndata)) return fail(FK_EINVAL, "ldo < ndata");
+    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
+    if (!(t->mask & FK_PREC_BIT(prec)))
+        return fail(FK_EUNSUPPORTED, "precision not stored in this table");
+    return FK_OK;
+}
+
+}  // namespace
+}  // namespace fk
+
+using namespace fk;
+
+extern "C" {
+
+const char *fk_strerror(int s) {
+    switch (s) {
+        case FK_OK: return "ok";
+        case FK_EINVAL: return "invalid argument";
+        case FK_ENOMEM: return "out of memory";
+        case FK_EBUDGET: return "request exceeds the memory budget";
+        case FK_EPENDING: return "request pending";
+        case FK_ETIMEDOUT: return "timed out";
+        case FK_ECUDA: return "CUDA error";
+        case FK_ENOTFOUND: return "not found";
+        case FK_EUNSUPPORTED: return "unsupported precision or table kind";
+        default: return "unknown status";
+    }
+}
+
+const char *fk_last_error_message(void) { return g_last_error.c_str(); }
+
+int fk_version(void) { return 100; }
+
+uint64_t fk_kernel_launches(void) { return g_launches.load(); }
+
+int fk_table_create_dis(const double *fk, int ndata, const int *flav, int nflav, int nx,
+                        const int *xmap, int nx_grid, unsigned prec_mask, fk_table **out) {
+    return table_create(FK_KIND_DIS, fk, ndata, flav, nullptr, nflav, nx, xmap, nx_grid, prec_mask, out);
+}
+
+int fk_table_create_had(const double *fk, int ndata, const int *ca, const int *cb, int nc, int nx,
+                        const int *xmap, int nx_grid, unsigned prec_mask, fk_table **out) {
+    return table_create(FK_KIND_HAD, fk, ndata, ca, cb, nc, nx, xmap, nx_grid, prec_mask, out);
+}
+
+int fk_table_destroy(fk_table *t) {
+    table_free(t);
+    return FK_OK;
+}
+
+int fk_table_info(const fk_table *t, int *kind, int *ndata, int *nchannels, int *nx, int *nx_grid,
+                  unsigned *prec_mask, size_t *device_bytes) {
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (kind) *kind = t->kind;
+    if (ndata) *ndata = t->ndata;
+    if (nchannels) *nchannels = t->nch;
+    if (nx) *nx = t->nx;
+    if (nx_grid) *nx_grid = t->nxg;
+    if (prec_mask) *prec_mask = t->mask;
+    if (device_bytes) *device_bytes = t->bytes;
+    return FK_OK;
+}
+
+int fk_dis_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
+                fk_stream stream) {
+    int rc = check_conv(t, FK_KIND_DIS, F, R, O, ldo, prec);
+    if (rc) return rc;
+    return fwd_cc(t, F, R, O, ldo ? ldo : t->ndata, prec == FK_FP64, (cudaStream_t)stream);
+}
+
+int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
+                fk_stream stream) {
+    int rc = check_conv(t, FK_KIND_HAD, F, R, O, ldo, prec);
+    if (rc) return rc;
+    ldo = ldo ? ldo : t->ndata;
+    if (prec == FK_FP64 || prec == FK_FP32)
+        return fwd_cc(t, F, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    return fwd_tc(t, (const float *)F, R, (float *)O, ldo, prec, (cudaStream_t)stream);
+}
+
+int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
+                     int accumulate, int prec, fk_stream stream) {
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (!gO || !gF || (t->kind == FK_KIND_HAD && !F)) return fail(FK_EINVAL, "null F, gO or gF");
+    if (R < 1) return fail(FK_EINVAL, "R < 1");
+    if (ldgo < 0 || (ldgo > 0 && ldgo < t->ndata)) return fail(FK_EINVAL, "ldgo < ndata");
+    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
+    if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
+    const bool f64 = prec == FK_FP64;
+    if (!f64 && !t->fk32)
+        return fail(FK_EUNSUPPORTED, "the adjoint in reduced modes needs the table's FP32 copy");
+    return bwd_cc(t, F, gO, ldgo ? ldgo : t->ndata, R, gF, accumulate ? 1 : 0, f64,
+                  (cudaStream_t)stream);
+}
+
+}  // extern "C"

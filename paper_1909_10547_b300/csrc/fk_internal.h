@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fk.h"
+
+namespace fk {
+
+constexpr int NFL = 14;
+constexpr int MAX_NX = 64;        // x points per table (stream kernels keep F in smem)
+constexpr int MAX_NXG = 64;       // points of the PDF grid
+constexpr int MAX_CH = NFL * NFL; // ordered flavour pairs
+
+// Thread-local error detail; returns the status for `return fail(...)`.
+int fail(int status, const std::string &msg);
+// Counts kernel launches (fk_kernel_launches); call once per <<<>>> launch.
+void count_launch(int n = 1);
+int cuda_fail(cudaError_t e, const char *what);
+#define FK_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ::fk::cuda_fail(e_, #call); \
+    } while (0)
+
+// Stream-ordered scratch memory for one call (cudaMallocAsync/cudaFreeAsync).
+struct Scratch {
+    cudaStream_t stream;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, stream);
+    }
+    template <typename T>
+    cudaError_t get(T **p, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 256, stream);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = reinterpret_cast<T *>(q);
+        return e;
+    }
+};
+
+// Tensor-core operand layout of a hadronic table (see k_tc.cu).
+struct TcLayout {
+    int ngroups = 0;                 // flavours a with at least one channel (a, b)
+    int grp_flav[NFL];               // flavour a of group g
+    int grp_nch[NFL];                // channels in group g
+    int grp_ch0[NFL];                // first entry of group g in grp_chan
+    int grp_kpad[NFL];               // K of group g padded to the K step
+    long long grp_koff[NFL];         // element offset of group g inside a tile
+    std::vector<int> grp_chan;       // channel ids ordered by group
+    int g = 0;                       // data points per N tile
+    int ntile_n = 0;                 // number of N tiles = ceil(ndata / g)
+    int n_rows = 0;                  // N of the MMA (g * nx rounded up to 16)
+    int ktot = 0;                    // sum of grp_kpad
+    long long tile_elems = 0;        // n_rows * ktot
+    int *d_grp = nullptr;            // device copy of the small per-group arrays
+};
+
+}  // namespace fk
+
+// Device-resident table.  Stream layouts keep the caller's element order
+// (channel, x_i, x_j) per data point, each row padded to ldE elements.
+struct fk_table {
+    int kind = 0;
+    int ndata = 0, nch = 0, nx = 0, nxg = 0;
+    long long E = 0;    // elements per data point
+    long long ldE = 0;  // padded row length
+    unsigned mask = 0;
+    int device = 0;
+    std::vector<int> ca, cb, xmap;  // host copies (DIS: ca = active flavours)
+    int *d_ca = nullptr, *d_cb = nullptr, *d_xmap = nullptr;
+    int *d_xinv = nullptr;          // [nxg] local x index of a grid point, or -1
+    double *fk64 = nullptr;         // [ndata][ldE]
+    float *fk32 = nullptr;          // [ndata][ldE]
+    // tensor-core layouts (hadronic): packed B operand tiles
+    fk::TcLayout tc;
+    __nv_bfloat16 *tc_hi = nullptr; // BF16 (or hi part)
+    __nv_bfloat16 *tc_lo = nullptr; // lo part (BF16X3)
+    float *tc_f32 = nullptr;        // TF32 operand (FP32 bits)
+    size_t bytes = 0;
+};
+
+// Plain view passed to kernels by value.
+struct TableView {
+    int ndata, nch, nx, nxg;
+    long long E, ldE;
+    const int *ca, *cb, *xmap, *xinv;
+};
+
+inline TableView view(const fk_table *t) {
+    return TableView{t->ndata, t->nch, t->nx, t->nxg, t->E, t->ldE,
+                     t->d_ca, t->d_cb, t->d_xmap, t->d_xinv};
+}
+
+namespace fk {
+// CUDA-core paths (k_cc.cu)
+int fwd_cc(const fk_table *t, const void *F, int R, void *O, int ldo, bool f64, cudaStream_t s);
+int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
+           int accumulate, bool f64, cudaStream_t s);
+// tensor-core path (k_tc.cu)
+int tc_build(fk_table *t, const double *host_fk);
+int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
+void tc_free(fk_table *t);
+// conversion helpers (k_cc.cu)
+int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
+                 float *d32, cudaStream_t s);
+}  // namespace fk

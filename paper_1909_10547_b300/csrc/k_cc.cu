@@ -1,0 +1,628 @@
+// CUDA-core kernels of the FK convolution in FP64 and FP32.
+//
+//  * k_stream : few replicas (R <= 4).  The observable is a dot product of the
+//    table row FK[d][.] with the weight vector w[e] (hadronic, Eq. 1:
+//    w[(c,i,j)] = f_{a_c}(x_i) f_{b_c}(x_j); DIS: w[(k,i)] = f_{a_k}(x_i)).
+//    The table is streamed once with 16-byte loads; each CTA owns an element
+//    chunk, keeps its weights in registers and reuses them over DB data points.
+//  * k_tile   : many replicas.  O[d][r] = sum_e FK[d][e] w[e][r] as a tiled
+//    product whose second operand is formed on the fly in shared memory from
+//    the two PDFs of the current channel (never materialised in HBM).
+//  * k_bwd_*  : the adjoint.  W[e][r] = sum_d FK[d][e] gO[r][d] is formed per
+//    tile, then contracted with the PDF of the other flavour of the channel
+//    (product rule on each term of Eq. 1).
+//
+// Reductions across CTAs never use atomics: every CTA writes its partial sums
+// to its own slot and a second kernel adds the slots in a fixed order, so the
+// result of a (d, r) pair does not depend on R, on the launch shape of other
+// replicas or on timing.
+#include "fk_internal.h"
+
+#include <algorithm>
+#include <mutex>
+#include <set>
+
+namespace fk {
+namespace {
+
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+    using t = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct V16<double> {
+    using t = double2;
+    static constexpr int n = 2;
+};
+
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
+
+__device__ __forceinline__ float dotv(float4 x, const float *w, float acc) {
+    acc = fmaf(x.x, w[0], acc);
+    acc = fmaf(x.y, w[1], acc);
+    acc = fmaf(x.z, w[2], acc);
+    return fmaf(x.w, w[3], acc);
+}
+__device__ __forceinline__ double dotv(double2 x, const double *w, double acc) {
+    acc = fma(x.x, w[0], acc);
+    return fma(x.y, w[1], acc);
+}
+
+template <typename T>
+struct SmemPdf {
+    T f[NFL * MAX_NXG];
+    int ca[MAX_CH], cb[MAX_CH], xm[MAX_NX];
+};
+
+template <int KIND, typename T>
+__device__ __forceinline__ T elem_weight(const SmemPdf<T> &s, long long e, const TableView &tv,
+                                         int nx2) {
+    if (e >= tv.E) return T(0);
+    const int ei = (int)e;
+    if (KIND == FK_KIND_HAD) {
+        const int c = ei / nx2;
+        const int rem = ei - c * nx2;
+        const int i = rem / tv.nx;
+        const int j = rem - i * tv.nx;
+        return s.f[s.ca[c] * tv.nxg + s.xm[i]] * s.f[s.cb[c] * tv.nxg + s.xm[j]];
+    } else {
+        const int k = ei / tv.nx;
+        const int i = ei - k * tv.nx;
+        return s.f[s.ca[k] * tv.nxg + s.xm[i]];
+    }
+}
+
+template <typename T>
+struct StreamCfg;
+template <>
+struct StreamCfg<float> {
+    static constexpr int U = 4, DB = 8;
+};
+template <>
+struct StreamCfg<double> {
+    static constexpr int U = 8, DB = 16;
+};
+
+// grid (nchunk, ceil(ndata/DB), R); part[(chunk * R + r) * ndata + d]
+template <int KIND, typename T>
+__global__ void __launch_bounds__(256) k_stream(TableView tv, const T *__restrict__ fk,
+                                                const T *__restrict__ F, int R,
+                                                T *__restrict__ part) {
+    using VT = typename V16<T>::t;
+    constexpr int V = V16<T>::n;
+    constexpr int U = StreamCfg<T>::U, DB = StreamCfg<T>::DB;
+    constexpr int CH = 256 * V * U;
+    __shared__ SmemPdf<T> s;
+    __shared__ T red[DB][256];
+    const int r = blockIdx.z;
+    const T *Fr = F + (size_t)r * NFL * tv.nxg;
+    for (int k = threadIdx.x; k < NFL * tv.nxg; k += 256) s.f[k] = Fr[k];
+    for (int k = threadIdx.x; k < tv.nch; k += 256) {
+        s.ca[k] = tv.ca[k];
+        if (KIND == FK_KIND_HAD) s.cb[k] = tv.cb[k];
+    }
+    for (int k = threadIdx.x; k < tv.nx; k += 256) s.xm[k] = tv.xmap[k];
+    __syncthreads();
+
+    const int nx2 = tv.nx * tv.nx;
+    const long long e0 = (long long)blockIdx.x * CH + threadIdx.x * V;
+    T w[U][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) w[u][v] = elem_weight<KIND>(s, e0 + u * 256 * V + v, tv, nx2);
+
+    const int d0 = blockIdx.y * DB;
+    T acc[DB];
+#pragma unroll
+    for (int dd = 0; dd < DB; ++dd) {
+        acc[dd] = T(0);
+        const int d = d0 + dd;
+        if (d < tv.ndata) {
+            const T *row = fk + (size_t)d * tv.ldE;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long e = e0 + u * 256 * V;
+                if (e < tv.ldE) acc[dd] = dotv(ld_stream(reinterpret_cast<const VT *>(row + e)), w[u], acc[dd]);
+            }
+        }
+    }
+#pragma unroll
+    for (int dd = 0; dd < DB; ++dd) red[dd][threadIdx.x] = acc[dd];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int dd = warp; dd < DB; dd += 8) {
+        T v = T(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v += red[dd][lane + 32 * k];
+#pragma unroll
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        const int d = d0 + dd;
+        if (lane == 0 && d < tv.ndata)
+            part[((size_t)blockIdx.x * R + r) * tv.ndata + d] = v;
+    }
+}
+
+// O[r][d] (+)= sum_k part[(k * R + r) * ndata + d], k ascending.
+template <typename T>
+__global__ void k_reduce_parts(const T *__restrict__ part, int nparts, int ndata, int R,
+                               T *__restrict__ O, int ldo) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * ndata) return;
+    const T *p = part + idx;
+    T s = T(0);
+    for (int k = 0; k < nparts; ++k) s += p[(size_t)k * R * ndata];
+    const long long r = idx / ndata, d = idx - r * ndata;
+    O[r * ldo + d] = s;
+}
+
+// ----------------------------------------------------------------------------
+// Many-replica tile kernel.
+// grid (ceil(ndata/64), ceil(R/64), nsplit); part[(split * R + r) * ndata + d]
+// ----------------------------------------------------------------------------
+template <typename T>
+struct TileCfg;
+template <>
+struct TileCfg<float> {
+    static constexpr int KC = 32;
+};
+template <>
+struct TileCfg<double> {
+    static constexpr int KC = 16;
+};
+constexpr int TDT = 64, TRT = 64;
+
+template <typename T>
+constexpr size_t tile_smem() {
+    return sizeof(T) * (TileCfg<T>::KC * (TDT + 1) + TileCfg<T>::KC * TRT + 2 * MAX_NX * TRT) +
+           sizeof(int) * (2 * MAX_CH + MAX_NX);
+}
+
+template <int KIND, typename T>
+__global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict__ fk,
+                                              const T *__restrict__ F, int R, int nsplit,
+                                              T *__restrict__ part) {
+    constexpr int KC = TileCfg<T>::KC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Bs = reinterpret_cast<T *>(smem_raw);  // [KC][TRT]
+    T *As = Bs + KC * TRT;                    // [KC][TDT + 1]
+    T *Fa = As + KC * (TDT + 1);              // [nx][TRT]
+    T *Fb = Fa + MAX_NX * TRT;                // [nx][TRT]
+    int *sca = reinterpret_cast<int *>(Fb + MAX_NX * TRT);
+    int *scb = sca + MAX_CH;
+    int *sxm = scb + MAX_CH;
+
+    const int d0 = blockIdx.x * TDT, r0 = blockIdx.y * TRT, sp = blockIdx.z;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int k = threadIdx.x; k < tv.nch; k += 256) {
+        sca[k] = tv.ca[k];
+        if (KIND == FK_KIND_HAD) scb[k] = tv.cb[k];
+    }
+    for (int k = threadIdx.x; k < tv.nx; k += 256) sxm[k] = tv.xmap[k];
+
+    T acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+
+    const size_t fstride = (size_t)NFL * tv.nxg;
+    const int nx2 = tv.nx * tv.nx;
+    // Segments: hadronic = channels (nx*nx elements each); DIS = one segment of
+    // E elements whose range is split instead.
+    int seg_b, seg_e;
+    long long el_b = 0, el_e = 0;
+    if (KIND == FK_KIND_HAD) {
+        seg_b = (int)((long long)tv.nch * sp / nsplit);
+        seg_e = (int)((long long)tv.nch * (sp + 1) / nsplit);
+    } else {
+        seg_b = 0;
+        seg_e = 1;
+        const long long nk = (tv.E + KC - 1) / KC;
+        el_b = nk * sp / nsplit * KC;
+        el_e = min(tv.E, nk * (sp + 1) / nsplit * KC);
+    }
+    __syncthreads();
+    for (int c = seg_b; c < seg_e; ++c) {
+        long long base, len;
+        if (KIND == FK_KIND_HAD) {
+            __syncthreads();
+            const int fa = sca[c], fb = scb[c];
+            for (int idx = threadIdx.x; idx < tv.nx * TRT; idx += 256) {
+                const int i = idx / TRT, rr = idx - i * TRT;
+                const int r = r0 + rr;
+                T va = T(0), vb = T(0);
+                if (r < R) {
+                    const T *Fr = F + (size_t)r * fstride;
+                    va = Fr[fa * tv.nxg + sxm[i]];
+                    vb = Fr[fb * tv.nxg + sxm[i]];
+                }
+                Fa[idx] = va;
+                Fb[idx] = vb;
+            }
+            __syncthreads();
+            base = (long long)c * nx2;
+            len = nx2;
+        } else {
+            base = el_b;
+            len = el_e - el_b;
+        }
+        for (long long k0 = 0; k0 < len; k0 += KC) {
+            for (int idx = threadIdx.x; idx < KC * TDT; idx += 256) {
+                const int kk = idx % KC, dd = idx / KC;
+                const int d = d0 + dd;
+                T v = T(0);
+                if (d < tv.ndata && k0 + kk < len) v = fk[(size_t)d * tv.ldE + base + k0 + kk];
+                As[kk * (TDT + 1) + dd] = v;
+            }
+            for (int idx = threadIdx.x; idx < KC * TRT; idx += 256) {
+                const int rr = idx % TRT, kk = idx / TRT;
+                T v = T(0);
+                if (k0 + kk < len) {
+                    if (KIND == FK_KIND_HAD) {
+                        const int k = (int)(k0 + kk);
+                        const int i = k / tv.nx, j = k - (k / tv.nx) * tv.nx;
+                        v = Fa[i * TRT + rr] * Fb[j * TRT + rr];
+                    } else if (r0 + rr < R) {
+                        const int e = (int)(base + k0 + kk);
+                        const int kf = e / tv.nx, i = e - kf * tv.nx;
+                        v = F[(size_t)(r0 + rr) * fstride + sca[kf] * tv.nxg + sxm[i]];
+                    }
+                }
+                Bs[kk * TRT + rr] = v;
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int kk = 0; kk < KC; ++kk) {
+                T a[4], b[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) a[p] = As[kk * (TDT + 1) + ty * 4 + p];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b[q] = Bs[kk * TRT + tx * 4 + q];
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int d = d0 + ty * 4 + p, r = r0 + tx * 4 + q;
+            if (d < tv.ndata && r < R) part[((size_t)sp * R + r) * tv.ndata + d] = acc[p][q];
+        }
+}
+
+// ----------------------------------------------------------------------------
+// Adjoint.  W[e][r] = sum_d FK[d][e] gO[r][d] over a tile of 128 elements x 64
+// replicas, K = data points.
+// ----------------------------------------------------------------------------
+constexpr int BET = 128, BRT = 64, BKD = 16;
+
+template <typename T>
+constexpr size_t bwd_smem() {
+    // As [BKD][BET], Gs [BKD][BRT], then Ws [BET][BRT+1] reuses As/Gs, plus
+    // Fa, Fb [MAX_NX][BRT]
+    size_t ab = sizeof(T) * (BKD * BET + BKD * BRT);
+    size_t w = sizeof(T) * BET * (BRT + 1);
+    return (ab > w ? ab : w) + sizeof(T) * 2 * MAX_NX * BRT;
+}
+
+// Accumulates the W tile for rows [e_b, e_b + rows) of the table, replicas
+// [r0, r0 + 64), into acc (thread (ty, tx) holds rows ty*8.., replicas tx*4..).
+template <typename T>
+__device__ __forceinline__ void bwd_w_tile(const TableView &tv, const T *__restrict__ fk,
+                                           const T *__restrict__ gO, int ldgo, int R, long long e_b,
+                                           int rows, int r0, T *As, T *Gs, T (&acc)[8][4]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int dk = 0; dk < tv.ndata; dk += BKD) {
+        for (int idx = threadIdx.x; idx < BKD * BET; idx += 256) {
+            const int e = idx % BET, kd = idx / BET;
+            const int d = dk + kd;
+            T v = T(0);
+            if (d < tv.ndata && e < rows) v = fk[(size_t)d * tv.ldE + e_b + e];
+            As[kd * BET + e] = v;
+        }
+        for (int idx = threadIdx.x; idx < BKD * BRT; idx += 256) {
+            const int kd = idx % BKD, rr = idx / BKD;
+            const int d = dk + kd, r = r0 + rr;
+            T v = T(0);
+            if (d < tv.ndata && r < R) v = gO[(size_t)r * ldgo + d];
+            Gs[kd * BRT + rr] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kd = 0; kd < BKD; ++kd) {
+            T a[8], b[4];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) a[p] = As[kd * BET + ty * 8 + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Gs[kd * BRT + tx * 4 + q];
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+}
+
+// Hadronic: grid (niblk, ceil(R/64), nch).  Each CTA covers rows i in
+// [i0, i0+ib) of channel c (ib*nx <= 128 contiguous elements).
+//   U[(c*R + r)*nx + i]              = sum_j W[c,i,j][r] f^r_{b_c}(x_j)
+//   Vp[((c*niblk + blk)*R + r)*nx + j] = sum_{i in blk} W[c,i,j][r] f^r_{a_c}(x_i)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_had(TableView tv, const T *__restrict__ fk,
+                                                 const T *__restrict__ F,
+                                                 const T *__restrict__ gO, int ldgo, int R,
+                                                 int IB, T *__restrict__ U, T *__restrict__ Vp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    size_t ab = sizeof(T) * (BKD * BET + BKD * BRT), w = sizeof(T) * BET * (BRT + 1);
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Gs = As + BKD * BET;
+    T *Ws = As;
+    T *Fa = reinterpret_cast<T *>(smem_raw + (ab > w ? ab : w));
+    T *Fb = Fa + MAX_NX * BRT;
+    const int blk = blockIdx.x, r0 = blockIdx.y * BRT, c = blockIdx.z;
+    const int niblk = gridDim.x;
+    const int i0 = blk * IB;
+    const int ib = min(IB, tv.nx - i0);
+    const int rows = ib * tv.nx;
+    const int nx2 = tv.nx * tv.nx;
+    const int fa = tv.ca[c], fb = tv.cb[c];
+    const size_t fstride = (size_t)NFL * tv.nxg;
+    for (int idx = threadIdx.x; idx < tv.nx * BRT; idx += 256) {
+        const int i = idx / BRT, rr = idx - i * BRT;
+        const int r = r0 + rr;
+        T va = T(0), vb = T(0);
+        if (r < R) {
+            const int x = tv.xmap[i];
+            va = F[(size_t)r * fstride + fa * tv.nxg + x];
+            vb = F[(size_t)r * fstride + fb * tv.nxg + x];
+        }
+        Fa[idx] = va;
+        Fb[idx] = vb;
+    }
+    T acc[8][4];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+    bwd_w_tile<T>(tv, fk, gO, ldgo, R, (long long)c * nx2 + (long long)i0 * tv.nx, rows, r0, As, Gs, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Ws[(ty * 8 + p) * (BRT + 1) + tx * 4 + q] = acc[p][q];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ib * BRT; idx += 256) {
+        const int il = idx / BRT, rr = idx - il * BRT;
+        const int r = r0 + rr;
+        T s = T(0);
+        for (int j = 0; j < tv.nx; ++j) s = fma(Ws[(il * tv.nx + j) * (BRT + 1) + rr], Fb[j * BRT + rr], s);
+        if (r < R) U[((size_t)c * R + r) * tv.nx + i0 + il] = s;
+    }
+    for (int idx = threadIdx.x; idx < tv.nx * BRT; idx += 256) {
+        const int j = idx / BRT, rr = idx - j * BRT;
+        const int r = r0 + rr;
+        T s = T(0);
+        for (int il = 0; il < ib; ++il)
+            s = fma(Ws[(il * tv.nx + j) * (BRT + 1) + rr], Fa[(i0 + il) * BRT + rr], s);
+        if (r < R) Vp[(((size_t)c * niblk + blk) * R + r) * tv.nx + j] = s;
+    }
+}
+
+// gF[r][a][m] (+)= sum_{c: ca=a} U[c][r][i(m)] + sum_{c: cb=a} sum_blk Vp[c][blk][r][i(m)]
+template <typename T>
+__global__ void k_bwd_had_gather(TableView tv, const T *__restrict__ U, const T *__restrict__ Vp,
+                                 int R, int niblk, int accumulate, T *__restrict__ gF) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)R * NFL * tv.nxg;
+    if (idx >= n) return;
+    const int m = (int)(idx % tv.nxg);
+    const int a = (int)((idx / tv.nxg) % NFL);
+    const int r = (int)(idx / ((long long)NFL * tv.nxg));
+    const int i = tv.xinv[m];
+    T s = T(0);
+    if (i >= 0) {
+        for (int c = 0; c < tv.nch; ++c) {
+            if (tv.ca[c] == a) s += U[((size_t)c * R + r) * tv.nx + i];
+            if (tv.cb[c] == a)
+                for (int b = 0; b < niblk; ++b) s += Vp[(((size_t)c * niblk + b) * R + r) * tv.nx + i];
+        }
+    }
+    gF[idx] = accumulate ? gF[idx] + s : s;
+}
+
+// DIS: grid (ceil(E/128), ceil(R/64)); gF[r][ca[k]][xmap[i]] += W[(k,i)][r].
+// gF must be zeroed beforehand when overwriting.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_dis(TableView tv, const T *__restrict__ fk,
+                                                 const T *__restrict__ gO, int ldgo, int R,
+                                                 T *__restrict__ gF) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *As = reinterpret_cast<T *>(smem_raw);
+    T *Gs = As + BKD * BET;
+    const long long e_b = (long long)blockIdx.x * BET;
+    const int rows = (int)min((long long)BET, tv.E - e_b);
+    const int r0 = blockIdx.y * BRT;
+    T acc[8][4];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+    bwd_w_tile<T>(tv, fk, gO, ldgo, R, e_b, rows, r0, As, Gs, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const size_t fstride = (size_t)NFL * tv.nxg;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const int e = ty * 8 + p;
+        if (e >= rows) continue;
+        const int eg = (int)(e_b + e);
+        const int k = eg / tv.nx, i = eg - k * tv.nx;
+        const int off = tv.ca[k] * tv.nxg + tv.xmap[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + tx * 4 + q;
+            if (r < R) gF[(size_t)r * fstride + off] += acc[p][q];
+        }
+    }
+}
+
+// FP64 rows (staging, [rows][E]) -> padded stream layouts.
+__global__ void k_convert(const double *__restrict__ src, long long rows, long long E,
+                          long long ldE, double *__restrict__ d64, float *__restrict__ d32) {
+    const long long n = rows * ldE;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long d = idx / ldE, e = idx - d * ldE;
+        const double v = e < E ? src[d * E + e] : 0.0;
+        if (d64) d64[idx] = v;
+        if (d32) d32[idx] = (float)v;
+    }
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per
+// process (so that later calls, including ones under stream capture, do not
+// repeat the attribute call).
+template <typename T, typename K>
+int set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return FK_OK;
+    static std::mutex mu;
+    static std::set<const void *> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count((const void *)kernel)) return FK_OK;
+    FK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert((const void *)kernel);
+    return FK_OK;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+template <int KIND, typename T>
+int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, cudaStream_t s) {
+    TableView tv = view(t);
+    Scratch scr(s);
+    T *part = nullptr;
+    int nparts;
+    if (R <= 4) {
+        constexpr int CH = 256 * V16<T>::n * StreamCfg<T>::U;
+        const int nchunk = (int)((t->ldE + CH - 1) / CH);
+        nparts = nchunk;
+        FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
+        dim3 grid(nchunk, (t->ndata + StreamCfg<T>::DB - 1) / StreamCfg<T>::DB, R);
+        k_stream<KIND, T><<<grid, 256, 0, s>>>(tv, fk, F, R, part);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    } else {
+        const int dt = (t->ndata + TDT - 1) / TDT, rt = (R + TRT - 1) / TRT;
+        const long long nseg = KIND == FK_KIND_HAD ? t->nch : (t->E + TileCfg<T>::KC - 1) / TileCfg<T>::KC;
+        // The split depends on the table only, so a replica's summation
+        // order does not change with R (bit-exact batching of requests).
+        long long want = (2LL * num_sms() + dt - 1) / dt;
+        nparts = (int)std::max(1LL, std::min(nseg, want));
+        FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
+        constexpr size_t smem = tile_smem<T>();
+        int rc = set_smem<T>(k_tile<KIND, T>, smem);
+        if (rc) return rc;
+        dim3 grid(dt, rt, nparts);
+        k_tile<KIND, T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    }
+    const long long n = (long long)R * t->ndata;
+    k_reduce_parts<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nparts, t->ndata, R, O, ldo);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+template <typename T>
+int bwd_cc_t(const fk_table *t, const T *F, const T *gO, int ldgo, int R, T *gF, int accumulate,
+             const T *fk, cudaStream_t s) {
+    TableView tv = view(t);
+    const int rt = (R + BRT - 1) / BRT;
+    constexpr size_t smem = bwd_smem<T>();
+    if (t->kind == FK_KIND_DIS) {
+        if (!accumulate) FK_CUDA(cudaMemsetAsync(gF, 0, sizeof(T) * (size_t)R * NFL * t->nxg, s));
+        int rc = set_smem<T>(k_bwd_dis<T>, smem);
+        if (rc) return rc;
+        dim3 grid((unsigned)((t->E + BET - 1) / BET), rt);
+        k_bwd_dis<T><<<grid, 256, smem, s>>>(tv, fk, gO, ldgo, R, gF);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+        return FK_OK;
+    }
+    Scratch scr(s);
+    const int IB = std::max(1, BET / t->nx);
+    const int niblk = (t->nx + IB - 1) / IB;
+    T *U = nullptr, *Vp = nullptr;
+    FK_CUDA(scr.get(&U, (size_t)t->nch * R * t->nx));
+    FK_CUDA(scr.get(&Vp, (size_t)t->nch * niblk * R * t->nx));
+    int rc = set_smem<T>(k_bwd_had<T>, smem);
+    if (rc) return rc;
+    dim3 grid(niblk, rt, t->nch);
+    k_bwd_had<T><<<grid, 256, smem, s>>>(tv, fk, F, gO, ldgo, R, IB, U, Vp);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    const long long n = (long long)R * NFL * t->nxg;
+    k_bwd_had_gather<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tv, U, Vp, R, niblk, accumulate, gF);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+}  // namespace
+
+int fwd_cc(const fk_table *t, const void *F, int R, void *O, int ldo, bool f64, cudaStream_t s) {
+    if (f64) {
+        if (!t->fk64) return fail(FK_EUNSUPPORTED, "table has no FP64 copy");
+        return t->kind == FK_KIND_HAD
+                   ? fwd_cc_t<FK_KIND_HAD, double>(t, (const double *)F, R, (double *)O, ldo, t->fk64, s)
+                   : fwd_cc_t<FK_KIND_DIS, double>(t, (const double *)F, R, (double *)O, ldo, t->fk64, s);
+    }
+    if (!t->fk32) return fail(FK_EUNSUPPORTED, "table has no FP32 copy");
+    return t->kind == FK_KIND_HAD
+               ? fwd_cc_t<FK_KIND_HAD, float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s)
+               : fwd_cc_t<FK_KIND_DIS, float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s);
+}
+
+int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
+           int accumulate, bool f64, cudaStream_t s) {
+    if (f64) {
+        if (!t->fk64) return fail(FK_EUNSUPPORTED, "table has no FP64 copy");
+        return bwd_cc_t<double>(t, (const double *)F, (const double *)gO, ldgo, R, (double *)gF,
+                                accumulate, t->fk64, s);
+    }
+    if (!t->fk32) return fail(FK_EUNSUPPORTED, "table has no FP32 copy");
+    return bwd_cc_t<float>(t, (const float *)F, (const float *)gO, ldgo, R, (float *)gF,
+                           accumulate, t->fk32, s);
+}
+
+int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
+                 float *d32, cudaStream_t s) {
+    const long long n = rows * ldE;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_convert<<<blocks, 256, 0, s>>>(d_src, rows, E, ldE, d64, d32);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+}  // namespace fk

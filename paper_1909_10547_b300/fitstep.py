@@ -1,0 +1,112 @@
+"""One gradient-descent fit step over a set of device-resident FK tables.
+
+The step is the hot path of the paper's fit (Sec. 2: gradient descent; Sec. 3:
+the convolution is the most time-consuming operation):
+
+  forward   O[:, off_k : off_k + n_k] = conv(table_k, F)   for every dataset k
+  loss      chi2[r] = (O_r - D)^T C^{-1} (O_r - D),  gO = d chi2 / d O  (FP64)
+  backward  gF = sum_k conv_backward(table_k, F, gO[:, off_k : off_k + n_k])
+
+All three run in libfk.so kernels on the current CUDA stream.  capture()
+records each phase in a CUDA graph so a step costs three graph launches.
+"""
+import numpy as np
+import torch
+
+from . import Cov, Table, chi2, conv, conv_backward, _lib
+
+NFL = 14
+
+
+class GlobalFit:
+    def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda"):
+        """tables: workloads.DisTable/HadTable list sharing one x grid;
+        F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
+        table; D: [sum ndata] pseudo-data."""
+        self.prec = prec
+        io = torch.float64 if prec == "fp64" else torch.float32
+        if store is None:
+            store = ("fp64", "fp32") if prec in ("fp64", "fp32") else ("fp32", prec)
+        self.tabs = []
+        for t in tables:
+            st = store if hasattr(t, "ca") else tuple(p for p in store if p in ("fp64", "fp32")) or ("fp32",)
+            self.tabs.append(Table.from_workload(t, st))
+        self.kinds = ["had" if hasattr(t, "ca") else "dis" for t in tables]
+        nd = [t.ndata for t in tables]
+        self.offs = np.concatenate([[0], np.cumsum(nd)]).astype(int)
+        self.ntot = int(self.offs[-1])
+        self.R = F.shape[0]
+        self.nxg = F.shape[2]
+        self.io = io
+        self.cov = Cov(cov_blocks)
+        assert self.cov.n == self.ntot
+        self.D = torch.tensor(np.asarray(D, np.float64), device=device)
+        self.F = torch.tensor(np.asarray(F), dtype=io, device=device)
+        self.O = torch.empty((self.R, self.ntot), dtype=io, device=device)
+        self.gO = torch.empty_like(self.O)
+        self.gF = torch.empty_like(self.F)
+        self.chi2 = torch.empty(self.R, dtype=torch.float64, device=device)
+        self.graphs = None
+        # algorithmic work per step (multiply-adds counted as 2 flops)
+        fwd = bwd = 0
+        for t in tables:
+            if hasattr(t, "ca"):
+                e = t.ndata * t.nc * t.nx * t.nx
+                fwd += 2 * e * self.R
+                bwd += (2 * e + 4 * t.nc * t.nx * t.nx) * self.R
+            else:
+                e = t.ndata * len(t.flav) * t.nx
+                fwd += 2 * e * self.R
+                bwd += 2 * e * self.R
+        self.flops = {"forward": fwd, "loss": 2 * int(sum(n * n for n in nd)) * self.R, "backward": bwd}
+        esz = 8 if prec == "fp64" else 4
+        self.table_bytes = {"forward": sum(t.ndata * (t.nc * t.nx * t.nx if hasattr(t, "ca") else len(t.flav) * t.nx)
+                                           for t in tables) * esz}
+
+    # -- phases ------------------------------------------------------------
+    def forward(self):
+        for k, t in enumerate(self.tabs):
+            conv(t, self.F, self.prec, out=self.O[:, self.offs[k]:self.offs[k + 1]])
+
+    def loss(self):
+        chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)
+
+    def backward(self):
+        bprec = self.prec if self.prec in ("fp64", "fp32") else "fp32"
+        for k, t in enumerate(self.tabs):
+            conv_backward(t, self.F, self.gO[:, self.offs[k]:self.offs[k + 1]], bprec,
+                          gF=self.gF, accumulate=k > 0)
+
+    def step(self):
+        if self.graphs is not None:
+            for g in self.graphs.values():
+                g.replay()
+        else:
+            self.forward()
+            self.loss()
+            self.backward()
+
+    def capture(self):
+        """Records the three phases in CUDA graphs (after one eager step)."""
+        self.forward()
+        self.loss()
+        self.backward()
+        torch.cuda.synchronize()
+        graphs = {}
+        for name, fn in (("forward", self.forward), ("loss", self.loss), ("backward", self.backward)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            graphs[name] = g
+        torch.cuda.synchronize()
+        self.graphs = graphs
+        return graphs
+
+    def launches_per_step(self):
+        """Kernels of this library one eager step launches."""
+        before = _lib.load().fk_kernel_launches()
+        g, self.graphs = self.graphs, None
+        self.step()
+        self.graphs = g
+        torch.cuda.synchronize()
+        return int(_lib.load().fk_kernel_launches() - before)

@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI: the library loads and exports every symbol
+include/fk.h declares; argument errors are caught before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1909_10547_b300 as fk
+from paper_1909_10547_b300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fk_\w+)\s*\(", src))
+    return names
+
+
+def test_header_declares_the_boundary():
+    need = {"fk_dis_conv", "fk_had_conv", "fk_conv_backward", "fk_chi2", "fk_serve_submit",
+            "fk_serve_poll", "fk_table_create_had", "fk_table_create_dis", "fk_cov_create"}
+    assert need <= declared()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    missing = [n for n in sorted(declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+    bound = set(_lib.SIGNATURES) | set(_lib.STRING_FUNCS) | set(_lib.U64_FUNCS)
+    assert declared() <= bound, declared() - bound
+
+
+def test_version_and_strerror():
+    lib = _lib.load()
+    assert lib.fk_version() >= 100
+    assert lib.fk_strerror(_lib.FK_EINVAL) == b"invalid argument"
+    assert lib.fk_strerror(12345) == b"unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(fk_shape=(0, 1, 3, 3)),                 # ndata < 1
+    dict(fk_shape=(1, 1, 65, 65)),               # nx too large
+    dict(ca=[14], cb=[0]),                       # flavour out of range
+    dict(ca=[1, 1], cb=[2, 2], fk_shape=(1, 2, 3, 3)),  # duplicate channel
+    dict(precs=()),                              # empty mask
+])
+def test_table_argument_errors_need_no_gpu(bad):
+    import numpy as np
+    shape = bad.get("fk_shape", (1, 1, 3, 3))
+    with pytest.raises(fk.FKError) as e:
+        fk.Table.had(np.zeros(shape), bad.get("ca", [0] * shape[1]), bad.get("cb", [1] * shape[1]),
+                     precs=bad.get("precs", ("fp32",)))
+    assert e.value.status == _lib.FK_EINVAL
+
+
+def test_null_pointer_calls_are_rejected():
+    lib = _lib.load()
+    assert lib.fk_had_conv(None, None, 1, None, 0, 0, None) == _lib.FK_EINVAL
+    assert lib.fk_conv_backward(None, None, None, 0, 1, None, 0, 0, None) == _lib.FK_EINVAL
+    assert lib.fk_chi2(None, None, None, 1, None, None, 0, None) == _lib.FK_EINVAL
+    assert lib.fk_table_destroy(None) == 0
+    assert lib.fk_cov_size(None) == 0

@@ -1,0 +1,63 @@
+"""FP64 chi^2 on the device vs the oracle (Cholesky-Banachiewicz + substitution)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1909_10547_b300 as fk
+from paper_1909_10547_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _blocks(sizes, seed):
+    rng = np.random.default_rng(seed)
+    o = [rng.uniform(0.5, 5.0, n) for n in sizes]
+    return W.covariance(o, seed), o
+
+
+@pytest.mark.parametrize("sizes,R", [([1], 1), ([2, 3], 2), ([31, 33, 64, 65], 33),
+                                     ([600, 10, 250], 100), ([17] * 40, 7)])
+def test_chi2_matches_oracle(sizes, R):
+    cov, o = _blocks(sizes, len(sizes) + R)
+    D = np.concatenate(W.pseudo_data(o, 5))
+    rng = np.random.default_rng(R)
+    O = np.concatenate(o)[None, :] * rng.uniform(0.9, 1.1, (R, sum(sizes)))
+    want = np.zeros(R)
+    g_want = np.zeros((R, sum(sizes)))
+    off = 0
+    for b in cov.blocks:
+        n = b.shape[0]
+        L = oracle.cholesky(b)
+        c, g = oracle.chi2(L, O[:, off:off + n], D[off:off + n])
+        want += c
+        g_want[:, off:off + n] = g
+        off += n
+    dc = fk.Cov(cov.blocks)
+    Od = torch.tensor(O, device="cuda")
+    Dd = torch.tensor(D, device="cuda")
+    c, g = fk.chi2(dc, Od, Dd)
+    torch.cuda.synchronize()
+    c, g = c.cpu().numpy(), g.cpu().numpy()
+    np.testing.assert_allclose(c, want, rtol=1e-12, atol=0)
+    scale = np.abs(g_want).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g - g_want) <= 1e-11 * scale)
+
+
+def test_chi2_zero_at_data_and_identity_cov():
+    n = 50
+    D = np.linspace(1, 2, n)
+    dc = fk.Cov([np.eye(n)])
+    O = np.stack([D, D + 1.0, D * 2])
+    c, g = fk.chi2(dc, torch.tensor(O, device="cuda"), torch.tensor(D, device="cuda"))
+    c, g = c.cpu().numpy(), g.cpu().numpy()
+    assert c[0] == 0.0 and np.all(g[0] == 0.0)
+    assert abs(c[1] - n) < 1e-12 * n
+    np.testing.assert_allclose(c[2], ((D) ** 2).sum(), rtol=1e-13)
+    np.testing.assert_allclose(g[2], 2 * D, rtol=1e-14)
+
+
+def test_cov_rejects_non_spd():
+    bad = np.array([[1.0, 2.0], [2.0, 1.0]])
+    with pytest.raises(fk.FKError, match="positive definite"):
+        fk.Cov([np.eye(3), bad])

@@ -92,6 +92,12 @@ int fk_version(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices); for accounting in benchmarks. */
 uint64_t fk_kernel_launches(void);
+/* Device-side health of the tensor-core kernels on the current device: every
+ * wait inside them (on a copy, an MMA or another warp) is bounded in time; if
+ * one ran out, the kernel stopped early, left its outputs incomplete and
+ * raised a flag.  Returns FK_ETIMEDOUT if the flag is set, else FK_OK; clears
+ * it if reset != 0.  Synchronises with the device (a blocking copy). */
+int fk_device_status(int reset);
 
 /* ---------------------------------------------------------------- tables */
 

@@ -15,6 +15,7 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 # name -> argtypes; every function returns int except the string getters.
 SIGNATURES = {
     "fk_version": [],
+    "fk_device_status": [I],
     "fk_table_create_dis": [P, I, P, I, I, P, I, U, PP],
     "fk_table_create_had": [P, I, P, P, I, I, P, I, U, PP],
     "fk_table_destroy": [P],

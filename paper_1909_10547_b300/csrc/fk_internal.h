@@ -1,8 +1,9 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
-#include <cuda_runtime.h>
+#include <cuda.h>  // CUtensorMap (types only; the driver is reached through cudart)
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -47,21 +48,32 @@ struct Scratch {
     }
 };
 
-// Tensor-core operand layout of a hadronic table (see k_tc.cu).
+// Channel groups of a hadronic table for the tensor-core path (k_tc.cu):
+// group g collects the channels (a_g, b) of one first flavour a_g.  Along the
+// contraction axis K the groups are concatenated, each padded to a multiple of
+// 16 elements; inside a group, K runs over (channel, x_j).
+struct TcGroups {
+    int ngroups;
+    int flav[NFL];    // a_g
+    int nch[NFL];     // channels in group g
+    int ch0[NFL];     // first entry of group g in chan[]
+    int kbeg[NFL];    // K range [kbeg, kend) of group g
+    int kend[NFL];
+    int chan[MAX_CH]; // channel ids ordered by group
+};
+
+// Tensor-core layout of a hadronic table: the B operand of the MMA, one tile
+// of n_rows rows per G data points, K-major with row length ktot_pad.
 struct TcLayout {
-    int ngroups = 0;                 // flavours a with at least one channel (a, b)
-    int grp_flav[NFL];               // flavour a of group g
-    int grp_nch[NFL];                // channels in group g
-    int grp_ch0[NFL];                // first entry of group g in grp_chan
-    int grp_kpad[NFL];               // K of group g padded to the K step
-    long long grp_koff[NFL];         // element offset of group g inside a tile
-    std::vector<int> grp_chan;       // channel ids ordered by group
-    int g = 0;                       // data points per N tile
-    int ntile_n = 0;                 // number of N tiles = ceil(ndata / g)
-    int n_rows = 0;                  // N of the MMA (g * nx rounded up to 16)
-    int ktot = 0;                    // sum of grp_kpad
-    long long tile_elems = 0;        // n_rows * ktot
-    int *d_grp = nullptr;            // device copy of the small per-group arrays
+    TcGroups grp{};
+    int G = 0;          // data points per tile (power of two, G * nx <= 256)
+    int ntile_n = 0;    // ceil(ndata / G)
+    int n_rows = 0;     // MMA N = G * nx rounded up to 16; row n = i * G + (d % G)
+    int ktot = 0;       // used K (sum of padded group lengths)
+    int ktot_pad = 0;   // row length, a multiple of 64
+    CUtensorMap map_hi;   // BF16 / hi part (the type is 128-byte aligned)
+    CUtensorMap map_lo;   // lo part
+    CUtensorMap map_f32;  // TF32 operand
 };
 
 }  // namespace fk
@@ -109,6 +121,8 @@ int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, vo
 int tc_build(fk_table *t, const double *host_fk);
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
 void tc_free(fk_table *t);
+// FK_ETIMEDOUT if a kernel's bounded wait ran out since the last reset
+int device_status(int reset);
 // conversion helpers (k_cc.cu)
 int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
                  float *d32, cudaStream_t s);

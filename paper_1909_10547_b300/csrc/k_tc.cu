@@ -1,10 +1,699 @@
-// Tensor-core path (tcgen05): placeholder until the kernel lands.
+// Many-replica hadronic convolution on the 5th-generation tensor cores
+// (tcgen05, sm_103a), with TMA operand staging and TMEM accumulators.
+//
+// Eq. 1 per data point d and replica r, with the channels grouped by their
+// first flavour a (group g, channels (a_g, b)):
+//
+//   O[r][d] = sum_g sum_i f^r_{a_g}(x_i) * Y_g[r][(i, d)],
+//   Y_g[r][(i, d)] = sum_{(c, j) in g} F_g[r][(c, j)] * FK[d][c][i][j],
+//   F_g[r][(c, j)] = f^r_{b_c}(x_j).
+//
+// Y_g is a dense product (M = replicas, N = (x_i, data point) rows of one
+// tile, K = the group's (channel, x_j) pairs) and runs on the tensor cores;
+// the Hadamard product with f^r_{a_g}(x_i) and the sum over i and g are fused
+// into the epilogue, which reads Y_g straight out of TMEM.  Each thread of the
+// epilogue owns one replica (one TMEM lane), so the reduction over (g, i) is a
+// fixed-order register accumulation with no atomics.
+//
+// Roles per CTA (192 threads, persistent over tiles):
+//   warp 0 lane 0 : TMA producer (A = packed PDF operand, B = packed table)
+//   warp 1 lane 0 : MMA issuer; warp 1 also allocates / frees TMEM
+//   warps 2..5    : epilogue, TMEM lane quarter (warp % 4)
+// Pipelines: an S-stage shared-memory ring (full/empty mbarriers) and two
+// 256-column TMEM accumulators (acc_full/acc_empty), so the epilogue of
+// group g overlaps the MMAs of group g+1.  Every wait is bounded by the
+// global timer; on time-out the CTA sets an error word, stops issuing work,
+// lets its copies land, frees TMEM and returns.
 #include "fk_internal.h"
 
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+#include <set>
+
 namespace fk {
-int tc_build(fk_table *, const double *) { return fail(FK_EUNSUPPORTED, "tensor-core modes not built yet"); }
-int fwd_tc(const fk_table *, const float *, int, float *, int, int, cudaStream_t) {
-    return fail(FK_EUNSUPPORTED, "tensor-core modes not built yet");
+
+__device__ int g_fk_device_error;  // non-zero after a bounded wait ran out
+
+namespace {
+
+constexpr int TC_M = 128;   // replicas per tile (MMA M)
+constexpr int TC_THREADS = 192;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr int KPAD = 16;    // K padding of each group (a multiple of both K steps)
+
+// ---------------------------------------------------------------- PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-void tc_free(fk_table *) {}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of the given parity; false if the CTA is aborting or
+// the wait ran out (then the abort flag is raised).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            atomicExch(&g_fk_device_error, 1);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
+// 8-row groups 1024 B apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accum) {
+    if (PREC == FK_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------ kernel ----
+template <int PREC>
+struct Tr {
+    static constexpr bool X3 = PREC == FK_BF16X3;
+    static constexpr int ESZ = PREC == FK_TF32 ? 4 : 2;
+    static constexpr int KC = 128 / ESZ;      // K elements per 128-byte swizzled row
+    static constexpr int KSTEP = 32 / ESZ;    // K per MMA instruction
+    static constexpr int NOPS = X3 ? 2 : 1;   // operand copies (hi, lo)
+    static constexpr int STAGES = X3 ? 2 : 4;
+    static constexpr uint32_t FMT = PREC == FK_TF32 ? 2u : 1u;  // TF32 : BF16
+};
+
+struct TcParams {
+    int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
+    int kbeg[NFL], kend[NFL];
+    const float *Fm;  // [ngroups][nx][R_pad] epilogue multipliers f^r_{a_g}(x_i)
+    float *O;
+};
+
+template <int PREC>
+size_t tc_smem_bytes(int n_rows) {
+    const size_t stage = (size_t)Tr<PREC>::NOPS * (TC_M * 128 + (size_t)n_rows * 128);
+    return 1024 + Tr<PREC>::STAGES * stage + 256;
+}
+
+template <int PREC, int G>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
+         const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
+         TcParams p) {
+    using T = Tr<PREC>;
+    constexpr int S = T::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)p.n_rows * 128;
+    const uint32_t stage_bytes = T::NOPS * (a_bytes + b_bytes);
+    const uint32_t bar0 = base + S * stage_bytes;
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 8u * (S + s); };
+    auto accf = [&](int b) { return bar0 + 8u * (2 * S + b); };
+    auto acce = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
+    const uint32_t drain = bar0 + 8u * (2 * S + 4);  // all MMAs of this CTA done
+    uint8_t *gen = smem_raw + (bar0 - raw) + 8 * (2 * S + 5);
+    volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(gen);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gen + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&mapA);
+        prefetch_map(&mapB);
+        if (T::X3) {
+            prefetch_map(&mapA2);
+            prefetch_map(&mapB2);
+        }
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32((const void *)tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------ TMA producer
+        int it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            const int rt = tile % p.nrt, nt = tile / p.nrt;
+            for (int q = 0; q < p.nchunks; ++q, ++it) {
+                const int s = it % S;
+                if (!mbar_wait(empty(s), ((it / S) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = base + s * stage_bytes;
+                mbar_expect_tx(full(s), stage_bytes);
+                tma_load_2d(st, &mapA, full(s), q * T::KC, rt * TC_M);
+                tma_load_2d(st + a_bytes, &mapB, full(s), q * T::KC, nt * p.n_rows);
+                if (T::X3) {
+                    tma_load_2d(st + a_bytes + b_bytes, &mapA2, full(s), q * T::KC, rt * TC_M);
+                    tma_load_2d(st + 2 * a_bytes + b_bytes, &mapB2, full(s), q * T::KC, nt * p.n_rows);
+                }
+            }
+        }
+        if (!ok) {
+            // let the copies already issued land before the CTA exits
+            for (int k = 1; k <= S && it - k >= 0; ++k) {
+                const int j = it - k;
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(full(j % S), (j / S) & 1) && gtimer() - t0 < WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t idesc = (1u << 4) | (T::FMT << 7) | (T::FMT << 10) |
+                               ((uint32_t)(p.n_rows >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        int it = 0, gc = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            int g = 0;
+            for (int q = 0; q < p.nchunks && ok; ++q, ++it) {
+                const int s = it % S;
+                if (!mbar_wait(full(s), (it / S) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = base + s * stage_bytes;
+                for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
+                    const int k = q * T::KC + ks * T::KSTEP;
+                    while (g < p.ngroups && k >= p.kend[g]) ++g;
+                    if (g >= p.ngroups) break;
+                    const int b = gc & 1;
+                    if (k == p.kbeg[g]) {
+                        if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const uint32_t d = tmem + (uint32_t)(b * 256);
+                    const uint32_t off = (uint32_t)ks * 32u;
+                    const uint64_t ah = sw128_desc(st + off);
+                    const uint64_t bh = sw128_desc(st + a_bytes + off);
+                    mma<PREC>(d, ah, bh, idesc, k != p.kbeg[g]);
+                    if (T::X3) {
+                        const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
+                        const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
+                        mma<PREC>(d, ah, bl, idesc, 1);
+                        mma<PREC>(d, al, bh, idesc, 1);
+                    }
+                    if (k + T::KSTEP == p.kend[g]) {
+                        mma_commit(accf(b));
+                        ++gc;
+                    }
+                }
+                mma_commit(empty(s));
+            }
+        }
+        // TMEM is freed only after every MMA issued here has completed
+        mma_commit(drain);
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(drain, 0)) {
+            if (gtimer() - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicExch(&g_fk_device_error, 1);
+                break;
+            }
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int rl = quarter * 32 + lane;
+        int gc = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+            const int rt = tile % p.nrt, nt = tile / p.nrt;
+            const int r = rt * TC_M + rl;
+            float acc[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) acc[u] = 0.f;
+            const int ncols = ((G * p.nx + 31) / 32) * 32;
+            for (int g = 0; g < p.ngroups; ++g, ++gc) {
+                const int b = gc & 1;
+                const float *fm = p.Fm + (size_t)g * p.nx * p.R_pad + r;
+                // one lane waits, the warp follows (tcgen05.ld is warp-collective)
+                int got = 1;
+                if (lane == 0) got = mbar_wait(accf(b), (gc >> 1) & 1, abort_flag);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+                for (int c0 = 0; c0 < ncols; c0 += 32) {
+                    float m[32 / G];
+#pragma unroll
+                    for (int u = 0; u < 32 / G; ++u) {
+                        const int i = c0 / G + u;
+                        m[u] = i < p.nx ? __ldg(fm + (size_t)i * p.R_pad) : 0.f;
+                    }
+                    uint32_t v[32];
+                    tmem_ld32(taddr + (uint32_t)c0, v);
+#pragma unroll
+                    for (int u = 0; u < 32 / G; ++u)
+#pragma unroll
+                        for (int dl = 0; dl < G; ++dl)
+                            acc[dl] = fmaf(m[u], __uint_as_float(v[u * G + dl]), acc[dl]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce(b));
+            }
+            if (!ok) break;
+            if (r < p.R) {
+#pragma unroll
+                for (int dl = 0; dl < G; ++dl) {
+                    const int dd = nt * G + dl;
+                    if (dd < p.ndata) p.O[(size_t)r * p.ldo + dd] = acc[dl];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// ------------------------------------------------------------ packing ----
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_op(long long idx, float v, __nv_bfloat16 *hi,
+                                         __nv_bfloat16 *lo, float *f32) {
+    if (PREC == FK_TF32) {
+        f32[idx] = tf32_rna(v);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[idx] = h;
+        if (PREC == FK_BF16X3) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// group of K index k (groups are contiguous and sorted); -1 past the last
+__device__ __forceinline__ int group_of(const TcGroups &gr, int k) {
+    for (int g = 0; g < gr.ngroups; ++g)
+        if (k < gr.kend[g]) return g;
+    return -1;
+}
+
+// A operand A[r][k] = f^r_{b_c}(x_j) for k = (channel c of its group, j), and
+// the epilogue multipliers Fm[g][i][r] = f^r_{a_g}(x_i).
+template <int PREC>
+__global__ void k_pack_pdf(const TcGroups gr, const int *__restrict__ cb, const int *__restrict__ xmap,
+                           int nx, int nxg, const float *__restrict__ F, int R, int R_pad, int ktot_pad,
+                           __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32, float *__restrict__ Fm) {
+    const long long nA = (long long)R_pad * ktot_pad;
+    const long long nM = (long long)gr.ngroups * nx * R_pad;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nA + nM;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (idx < nA) {
+            const int r = (int)(idx / ktot_pad), k = (int)(idx % ktot_pad);
+            float v = 0.f;
+            const int g = group_of(gr, k);
+            if (r < R && g >= 0) {
+                const int q = (k - gr.kbeg[g]) / nx, j = (k - gr.kbeg[g]) % nx;
+                if (q < gr.nch[g]) {
+                    const int c = gr.chan[gr.ch0[g] + q];
+                    v = F[((size_t)r * NFL + cb[c]) * nxg + xmap[j]];
+                }
+            }
+            store_op<PREC>(idx, v, hi, lo, f32);
+        } else {
+            const long long m = idx - nA;
+            const int r = (int)(m % R_pad);
+            const int i = (int)((m / R_pad) % nx);
+            const int g = (int)(m / ((long long)R_pad * nx));
+            Fm[m] = r < R ? F[((size_t)r * NFL + gr.flav[g]) * nxg + xmap[i]] : 0.f;
+        }
+    }
+}
+
+// B operand from the FP64 table [ndata][nc][nx][nx]: row nt * n_rows + i * G + dl
+// holds data point d = nt * G + dl at x_i; column k = (channel of its group, x_j).
+template <int PREC>
+__global__ void k_pack_table(const TcGroups gr, const double *__restrict__ fk, int ndata, int nc,
+                             int nx, int G, int n_rows, int ntile_n, int ktot_pad,
+                             __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+    const long long n = (long long)ntile_n * n_rows * ktot_pad;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long row = idx / ktot_pad;
+        const int k = (int)(idx % ktot_pad);
+        const int nt = (int)(row / n_rows), nr = (int)(row % n_rows);
+        const int i = nr / G, dl = nr % G;
+        const int d = nt * G + dl;
+        float v = 0.f;
+        const int g = group_of(gr, k);
+        if (i < nx && d < ndata && g >= 0) {
+            const int q = (k - gr.kbeg[g]) / nx, j = (k - gr.kbeg[g]) % nx;
+            if (q < gr.nch[g]) {
+                const int c = gr.chan[gr.ch0[g] + q];
+                v = (float)fk[(((size_t)d * nc + c) * nx + i) * nx + j];
+            }
+        }
+        store_op<PREC>(idx, v, hi, lo, f32);
+    }
+}
+
+// ------------------------------------------------------------ host ----
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+// 2-D K-major operand [rows][cols] with 128-byte swizzled boxes of
+// (128 B) x box_rows.
+int make_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_rows) {
+    auto fn = encoder();
+    if (!fn) return fail(FK_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return FK_OK;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+}
+
+template <typename K>
+int opt_in_smem(K kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<const void *> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count((const void *)kernel)) return FK_OK;
+    FK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert((const void *)kernel);
+    return FK_OK;
+}
+
+template <int PREC, int G>
+int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
+              const CUtensorMap &mB2, const TcParams &p, cudaStream_t s) {
+    const size_t smem = tc_smem_bytes<PREC>(t->tc.n_rows);
+    // opt in once at the largest tile (n_rows = 256) so that every table fits
+    int rc = opt_in_smem(k_tc<PREC, G>, tc_smem_bytes<PREC>(256));
+    if (rc) return rc;
+    const int grid = std::min(p.ntiles, sm_count());
+    k_tc<PREC, G><<<grid, TC_THREADS, smem, s>>>(mA, mA2, mB, mB2, p);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+template <int PREC>
+int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    Scratch scr(s);
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    float *f32 = nullptr, *Fm = nullptr;
+    const size_t nA = (size_t)R_pad * L.ktot_pad;
+    if (PREC == FK_TF32) {
+        FK_CUDA(scr.get(&f32, nA));
+    } else {
+        FK_CUDA(scr.get(&hi, nA));
+        if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
+    }
+    FK_CUDA(scr.get(&Fm, (size_t)L.grp.ngroups * t->nx * R_pad));
+    {
+        const long long n = (long long)nA + (long long)L.grp.ngroups * t->nx * R_pad;
+        const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 8);
+        k_pack_pdf<PREC><<<blocks, 256, 0, s>>>(L.grp, t->d_cb, t->d_xmap, t->nx, t->nxg, F, R, R_pad,
+                                                L.ktot_pad, hi, lo, f32, Fm);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    }
+    CUtensorMap mA, mA2;
+    const int esz = Tr<PREC>::ESZ;
+    int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, L.ktot_pad, R_pad, TC_M);
+    if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, L.ktot_pad, R_pad, TC_M);
+    if (rc) return rc;
+    if (PREC != FK_BF16X3) mA2 = mA;
+    const CUtensorMap &mB = PREC == FK_TF32 ? L.map_f32 : L.map_hi;
+    const CUtensorMap &mB2 = PREC == FK_BF16X3 ? L.map_lo : mB;
+
+    TcParams p{};
+    p.nrt = R_pad / TC_M;
+    p.ntiles = L.ntile_n * p.nrt;
+    p.nchunks = L.ktot_pad / Tr<PREC>::KC;
+    p.n_rows = L.n_rows;
+    p.ngroups = L.grp.ngroups;
+    p.nx = t->nx;
+    p.ndata = t->ndata;
+    p.R = R;
+    p.R_pad = R_pad;
+    p.ldo = ldo;
+    for (int g = 0; g < L.grp.ngroups; ++g) {
+        p.kbeg[g] = L.grp.kbeg[g];
+        p.kend[g] = L.grp.kend[g];
+    }
+    p.Fm = Fm;
+    p.O = O;
+    switch (L.G) {
+        case 4: return launch_tc<PREC, 4>(t, mA, mA2, mB, mB2, p, s);
+        case 8: return launch_tc<PREC, 8>(t, mA, mA2, mB, mB2, p, s);
+        case 16: return launch_tc<PREC, 16>(t, mA, mA2, mB, mB2, p, s);
+    }
+    return fail(FK_EINVAL, "bad tile height");
+}
+
+template <int PREC>
+int pack_table(fk_table *t, const double *d_fk, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const long long n = (long long)L.ntile_n * L.n_rows * L.ktot_pad;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 32);
+    k_pack_table<PREC><<<blocks, 256, 0, s>>>(L.grp, d_fk, t->ndata, t->nch, t->nx, L.G, L.n_rows,
+                                              L.ntile_n, L.ktot_pad, t->tc_hi, t->tc_lo, t->tc_f32);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+}  // namespace
+
+int tc_build(fk_table *t, const double *host_fk) {
+    TcLayout &L = t->tc;
+    TcGroups &gr = L.grp;
+    gr.ngroups = 0;
+    int k = 0, pos = 0;
+    for (int a = 0; a < NFL; ++a) {
+        int n = 0;
+        for (int c = 0; c < t->nch; ++c)
+            if (t->ca[c] == a) {
+                if (!n) {
+                    gr.flav[gr.ngroups] = a;
+                    gr.ch0[gr.ngroups] = pos;
+                    gr.kbeg[gr.ngroups] = k;
+                }
+                gr.chan[pos++] = c;
+                ++n;
+            }
+        if (n) {
+            gr.nch[gr.ngroups] = n;
+            k += (n * t->nx + KPAD - 1) / KPAD * KPAD;
+            gr.kend[gr.ngroups] = k;
+            ++gr.ngroups;
+        }
+    }
+    L.ktot = k;
+    L.ktot_pad = (k + 63) / 64 * 64;
+    L.G = t->nx <= 16 ? 16 : (t->nx <= 32 ? 8 : 4);
+    L.n_rows = (L.G * t->nx + 15) / 16 * 16;
+    L.ntile_n = (t->ndata + L.G - 1) / L.G;
+    const size_t elems = (size_t)L.ntile_n * L.n_rows * L.ktot_pad;
+    const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
+    const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
+    const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
+    if ((want_hi && cudaMalloc(&t->tc_hi, elems * 2)) || (want_lo && cudaMalloc(&t->tc_lo, elems * 2)) ||
+        (want_f32 && cudaMalloc(&t->tc_f32, elems * 4)))
+        return fail(FK_ENOMEM, "tensor-core table storage");
+    t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+
+    // full FP64 copy on the device for the packing kernels, then freed
+    const double *d_src = nullptr;
+    double *owned = nullptr;
+    cudaStream_t s = nullptr;
+    FK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int rc = FK_OK;
+    const size_t src_elems = (size_t)t->ndata * t->E;
+    if (cudaMalloc(&owned, src_elems * 8)) {
+        cudaStreamDestroy(s);
+        return fail(FK_ENOMEM, "tensor-core packing staging");
+    }
+    d_src = owned;
+    cudaError_t e = cudaMemcpyAsync(owned, host_fk, src_elems * 8, cudaMemcpyHostToDevice, s);
+    if (e) rc = cuda_fail(e, "tensor-core table upload");
+    if (!rc && want_f32) rc = pack_table<FK_TF32>(t, d_src, s);
+    if (!rc && want_lo) rc = pack_table<FK_BF16X3>(t, d_src, s);
+    else if (!rc && want_hi) rc = pack_table<FK_BF16>(t, d_src, s);
+    if (!rc) {
+        e = cudaStreamSynchronize(s);
+        if (e) rc = cuda_fail(e, "tensor-core table packing");
+    }
+    cudaFree(owned);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    const long long rows = (long long)L.ntile_n * L.n_rows;
+    if (want_hi && (rc = make_map(&L.map_hi, t->tc_hi, 2, L.ktot_pad, rows, L.n_rows))) return rc;
+    if (want_lo && (rc = make_map(&L.map_lo, t->tc_lo, 2, L.ktot_pad, rows, L.n_rows))) return rc;
+    if (want_f32 && (rc = make_map(&L.map_f32, t->tc_f32, 4, L.ktot_pad, rows, L.n_rows))) return rc;
+    return FK_OK;
+}
+
+int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s) {
+    if (t->kind != FK_KIND_HAD) return fail(FK_EUNSUPPORTED, "tensor-core modes need a hadronic table");
+    switch (prec) {
+        case FK_BF16: return fwd_tc_t<FK_BF16>(t, F, R, O, ldo, s);
+        case FK_BF16X3: return fwd_tc_t<FK_BF16X3>(t, F, R, O, ldo, s);
+        case FK_TF32: return fwd_tc_t<FK_TF32>(t, F, R, O, ldo, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
+}
+
+void tc_free(fk_table *t) {
+    cudaFree(t->tc_hi);
+    cudaFree(t->tc_lo);
+    cudaFree(t->tc_f32);
+    t->tc_hi = t->tc_lo = nullptr;
+    t->tc_f32 = nullptr;
+}
+
+int device_status(int reset) {
+    int v = 0;
+    FK_CUDA(cudaMemcpyFromSymbol(&v, g_fk_device_error, sizeof(int)));
+    if (reset) {
+        const int z = 0;
+        FK_CUDA(cudaMemcpyToSymbol(g_fk_device_error, &z, sizeof(int)));
+    }
+    return v ? FK_ETIMEDOUT : FK_OK;
+}
+
 }  // namespace fk

@@ -151,6 +151,31 @@ int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
                 fk_stream stream);
 
 /*
+ * fk_had_conv for FK_FP64 and FK_FP32 without any device allocation.  The
+ * paper has no counterpart to this entry point: it exists for callers that
+ * may not allocate device memory while they run (for example an application
+ * whose GPU memory is entirely owned by its own allocator or capped by a pool
+ * limit, or a latency-critical loop in which an allocation could wait on the
+ * driver).  Arguments, layouts and results are those of fk_had_conv.
+ *  - Temporary partial sums go to one static device array of 8 MiB that every
+ *    GPU loading this library reserves until the process exits.  A call whose
+ *    partial sums do not fit (roughly R * ndata * ceil(E / 4096) values for
+ *    R <= 4, R * ndata * min(nc, ~300 / ceil(ndata / 64)) values otherwise, of
+ *    8 or 4 bytes; E = nc * nx * nx) returns FK_EINVAL and says how many bytes
+ *    it needed; split the replicas over several calls.
+ *  - The first call on each device looks up the array's device address (a
+ *    one-time set-up); make that first call before any stream capture.
+ *  - All calls share the array and nothing is carried from one call to the
+ *    next; calls whose work overlaps on the GPU (for example on two streams
+ *    with no ordering between them) race on it and give wrong results, so
+ *    order them on one stream or with events.
+ * Errors: FK_EINVAL (as fk_had_conv, or scratch too small), FK_EUNSUPPORTED
+ * (reduced modes, or precision not stored), FK_ECUDA.
+ */
+int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
+                        fk_stream stream);
+
+/*
  * Adjoint of the convolution (the gradient of Sec. 3 / Table 1):
  *   gF[r][a][xmap[i]] (+)= sum_d gO[r][d] * dO[r][d] / df^r_a(x_i)
  * for either table kind.  F: DEVICE [R][14][nx_grid]; gO: DEVICE, replica

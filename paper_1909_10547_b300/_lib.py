@@ -22,6 +22,7 @@ SIGNATURES = {
     "fk_table_info": [P, P, P, P, P, P, P, P],
     "fk_dis_conv": [P, P, I, P, I, I, P],
     "fk_had_conv": [P, P, I, P, I, I, P],
+    "fk_had_conv_noalloc": [P, P, I, P, I, I, P],
     "fk_conv_backward": [P, P, P, I, I, P, I, I, P],
     "fk_cov_create": [P, P, I, PP],
     "fk_cov_destroy": [P],

@@ -626,3 +626,108 @@ int convert_rows(const double *d_src, long long rows, long long E, long long ldE
 }
 
 }  // namespace fk
+
+// ----------------------------------------------------------------------------
+// Allocation-free hadronic forward (fk_had_conv_noalloc).
+//
+// Some callers may not allocate device memory while they run: their device
+// memory is entirely owned by another allocator or capped by a pool limit, or
+// they sit in a latency-critical loop where any allocation could wait on the
+// driver.  For them the FP64/FP32 hadronic convolution is offered with its
+// temporary partial sums in the fixed array below instead of stream-ordered
+// scratch.  The array is reserved on every GPU that loads this library, for
+// the life of the process.  Host code must not use its name as a pointer (on
+// the host it is only a stand-in for the symbol): the device address is looked
+// up once per device with cudaGetSymbolAddress and passed to the kernels.
+// ----------------------------------------------------------------------------
+constexpr size_t FK_NOALLOC_BYTES = 8u << 20;  // 8 MiB of partial sums
+static __device__ __align__(256) unsigned char g_fk_noalloc_scratch[FK_NOALLOC_BYTES];
+
+namespace fk {
+namespace {
+
+// Device address of g_fk_noalloc_scratch on the current device.  The first
+// call on a device performs the lookup (so make it before any stream capture).
+int noalloc_scratch(void **out) {
+    static std::mutex mu;
+    static void *addr[256] = {};
+    int dev = 0;
+    FK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(FK_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_fk_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return FK_OK;
+}
+
+// Same launches as the FP64/FP32 hadronic forward, with the partial sums in
+// the static array.  Every partial-sum slot the reduction reads is written by
+// the first kernel of the same call, so nothing has to be cleared between
+// calls.
+template <typename T>
+int had_noalloc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, cudaStream_t s) {
+    TableView tv = view(t);
+    int nparts;
+    if (R <= 4) {
+        constexpr int CH = 256 * V16<T>::n * StreamCfg<T>::U;
+        nparts = (int)((t->ldE + CH - 1) / CH);
+    } else {
+        const int dt = (t->ndata + TDT - 1) / TDT;
+        const long long want = (2LL * num_sms() + dt - 1) / dt;
+        nparts = (int)std::max(1LL, std::min((long long)t->nch, want));
+    }
+    const size_t need = sizeof(T) * (size_t)nparts * R * t->ndata;
+    if (need > FK_NOALLOC_BYTES)
+        return fail(FK_EINVAL, "fk_had_conv_noalloc: this call needs " + std::to_string(need) +
+                                   " bytes of partial sums; the static area holds " +
+                                   std::to_string(FK_NOALLOC_BYTES) + " (use fewer replicas per call)");
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    T *part = static_cast<T *>(scratch);
+    if (R <= 4) {
+        dim3 grid(nparts, (t->ndata + StreamCfg<T>::DB - 1) / StreamCfg<T>::DB, R);
+        k_stream<FK_KIND_HAD, T><<<grid, 256, 0, s>>>(tv, fk, F, R, part);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    } else {
+        constexpr size_t smem = tile_smem<T>();
+        rc = set_smem<T>(k_tile<FK_KIND_HAD, T>, smem);
+        if (rc) return rc;
+        dim3 grid((t->ndata + TDT - 1) / TDT, (R + TRT - 1) / TRT, nparts);
+        k_tile<FK_KIND_HAD, T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    }
+    const long long n = (long long)R * t->ndata;
+    k_reduce_parts<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nparts, t->ndata, R, O, ldo);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+}  // namespace
+}  // namespace fk
+
+extern "C" int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ldo,
+                                   int prec, fk_stream stream) {
+    using namespace fk;
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (t->kind != FK_KIND_HAD) return fail(FK_EINVAL, "fk_had_conv_noalloc needs a hadronic table");
+    if (!F || !O) return fail(FK_EINVAL, "null F or O");
+    if (R < 1) return fail(FK_EINVAL, "R < 1");
+    if (ldo < 0 || (ldo > 0 && ldo < t->ndata)) return fail(FK_EINVAL, "ldo < ndata");
+    if (prec != FK_FP64 && prec != FK_FP32)
+        return fail(FK_EUNSUPPORTED, "fk_had_conv_noalloc offers FK_FP64 and FK_FP32 only");
+    if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
+    const cudaStream_t s = (cudaStream_t)stream;
+    ldo = ldo ? ldo : t->ndata;
+    if (prec == FK_FP64)
+        return had_noalloc_t<double>(t, (const double *)F, R, (double *)O, ldo, t->fk64, s);
+    return had_noalloc_t<float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s);
+}

@@ -73,20 +73,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the phase of the given parity; false if the CTA is aborting or
-// the wait ran out (then the abort flag is raised).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+// Waits for the phase of the given parity, polling only the barrier (the
+// hardware suspends the thread between polls).  Gives up after WAIT_NS and
+// raises the device error word; `dead` latches per thread, so after one
+// time-out a role stops waiting at once and the CTA drains within a few
+// time-outs instead of waiting on every remaining barrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, bool &dead) {
     if (mbar_try(bar, parity)) return true;
+    if (dead) return false;
     const uint64_t t0 = gtimer();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
+    while (!mbar_try(bar, parity)) {
         if (gtimer() - t0 > WAIT_NS) {
-            *abort_flag = 1;
+            dead = true;
             atomicExch(&g_fk_device_error, 1);
             return false;
         }
     }
+    return true;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int x, int y) {
@@ -196,9 +199,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t drain = bar0 + 8u * (2 * S + 4);  // all MMAs of this CTA done
     uint8_t *gen = smem_raw + (bar0 - raw) + 8 * (2 * S + 5);
     volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(gen);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(gen + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool dead = false;  // this thread's waits have timed out once
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full(s), 1);
@@ -209,7 +212,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(acce(b), 4);
         }
         mbar_init(drain, 1);
-        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         prefetch_map(&mapA);
         prefetch_map(&mapB);
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int rt = tile % p.nrt, nt = tile / p.nrt;
             for (int q = 0; q < p.nchunks; ++q, ++it) {
                 const int s = it % S;
-                if (!mbar_wait(empty(s), ((it / S) & 1) ^ 1, abort_flag)) {
+                if (!mbar_wait(empty(s), ((it / S) & 1) ^ 1, dead)) {
                     ok = false;
                     break;
                 }
@@ -267,22 +269,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int it = 0, gc = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            int g = 0;
+            // the current group's K range lives in registers; the parameter
+            // arrays are read only when a group ends
+            int g = 0, kb = p.kbeg[0], ke = p.kend[0];
             for (int q = 0; q < p.nchunks && ok; ++q, ++it) {
                 const int s = it % S;
-                if (!mbar_wait(full(s), (it / S) & 1, abort_flag)) {
+                if (!mbar_wait(full(s), (it / S) & 1, dead)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t st = base + s * stage_bytes;
+#pragma unroll
                 for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
                     const int k = q * T::KC + ks * T::KSTEP;
-                    while (g < p.ngroups && k >= p.kend[g]) ++g;
-                    if (g >= p.ngroups) break;
+                    if (g >= p.ngroups) break;  // K padding after the last group
                     const int b = gc & 1;
-                    if (k == p.kbeg[g]) {
-                        if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, abort_flag)) {
+                    if (k == kb) {
+                        if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, dead)) {
                             ok = false;
                             break;
                         }
@@ -292,16 +296,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t off = (uint32_t)ks * 32u;
                     const uint64_t ah = sw128_desc(st + off);
                     const uint64_t bh = sw128_desc(st + a_bytes + off);
-                    mma<PREC>(d, ah, bh, idesc, k != p.kbeg[g]);
+                    mma<PREC>(d, ah, bh, idesc, k != kb);
                     if (T::X3) {
                         const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
                         const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
                         mma<PREC>(d, ah, bl, idesc, 1);
                         mma<PREC>(d, al, bh, idesc, 1);
                     }
-                    if (k + T::KSTEP == p.kend[g]) {
+                    if (k + T::KSTEP == ke) {
                         mma_commit(accf(b));
                         ++gc;
+                        ++g;
+                        if (g < p.ngroups) {
+                            kb = p.kbeg[g];
+                            ke = p.kend[g];
+                        }
                     }
                 }
                 mma_commit(empty(s));
@@ -312,7 +321,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint64_t t0 = gtimer();
         while (!mbar_try(drain, 0)) {
             if (gtimer() - t0 > WAIT_NS) {
-                *abort_flag = 1;
                 atomicExch(&g_fk_device_error, 1);
                 break;
             }
@@ -330,12 +338,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int u = 0; u < G; ++u) acc[u] = 0.f;
             const int ncols = ((G * p.nx + 31) / 32) * 32;
+            constexpr int MI = 256 / G;  // x points a 256-column accumulator can hold
             for (int g = 0; g < p.ngroups; ++g, ++gc) {
                 const int b = gc & 1;
+                // the multipliers f^r_{a_g}(x_i) do not depend on the MMA:
+                // fetch them all before waiting so their latency overlaps it
                 const float *fm = p.Fm + (size_t)g * p.nx * p.R_pad + r;
+                float m[MI];
+#pragma unroll
+                for (int i = 0; i < MI; ++i) m[i] = i < p.nx ? __ldg(fm + (size_t)i * p.R_pad) : 0.f;
                 // one lane waits, the warp follows (tcgen05.ld is warp-collective)
                 int got = 1;
-                if (lane == 0) got = mbar_wait(accf(b), (gc >> 1) & 1, abort_flag);
+                if (lane == 0) got = mbar_wait(accf(b), (gc >> 1) & 1, dead);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -343,20 +357,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-                for (int c0 = 0; c0 < ncols; c0 += 32) {
-                    float m[32 / G];
 #pragma unroll
-                    for (int u = 0; u < 32 / G; ++u) {
-                        const int i = c0 / G + u;
-                        m[u] = i < p.nx ? __ldg(fm + (size_t)i * p.R_pad) : 0.f;
+                for (int c = 0; c < 8; ++c) {
+                    if (c * 32 < ncols) {
+                        uint32_t v[32];
+                        tmem_ld32(taddr + (uint32_t)(c * 32), v);
+#pragma unroll
+                        for (int u = 0; u < 32 / G; ++u)
+#pragma unroll
+                            for (int dl = 0; dl < G; ++dl)
+                                acc[dl] = fmaf(m[c * (32 / G) + u], __uint_as_float(v[u * G + dl]), acc[dl]);
                     }
-                    uint32_t v[32];
-                    tmem_ld32(taddr + (uint32_t)c0, v);
-#pragma unroll
-                    for (int u = 0; u < 32 / G; ++u)
-#pragma unroll
-                        for (int dl = 0; dl < G; ++dl)
-                            acc[dl] = fmaf(m[u], __uint_as_float(v[u * G + dl]), acc[dl]);
                 }
                 tc_fence_before();
                 __syncwarp();

@@ -19,7 +19,7 @@ import torch
 from . import _lib
 from ._lib import FKError, PRECS
 
-__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "Cov", "chi2", "FKConv",
+__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "Cov", "chi2", "FKConv", "Server",
            "FKError", "PRECS", "lib_path"]
 
 NFL = 14
@@ -209,6 +209,81 @@ def chi2(cov: Cov, O: torch.Tensor, D: torch.Tensor, grad=True, out=None, gO=Non
         g = gO if gO is not None else torch.empty_like(O)
     _lib.call("fk_chi2", cov.handle, _p(O), _p(D), R, _p(c), _p(g), io, _stream())
     return c, g
+
+
+class Server:
+    """Continuously batched serving over device-resident tables (fk_serve_*)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 4):
+        h = ctypes.c_void_p()
+        _lib.call("fk_serve_create", ctypes.c_size_t(int(budget_bytes)), int(max_inflight),
+                  ctypes.byref(h))
+        self._h = h
+        self._tables = []
+        self._meta = {}
+
+    def add_table(self, t: Table) -> int:
+        tid = ctypes.c_int()
+        _lib.call("fk_serve_add_table", self._h, t.handle, ctypes.byref(tid))
+        self._tables.append(t)
+        return tid.value
+
+    def submit(self, table_id: int, F: np.ndarray, prec="fp32") -> int:
+        """F: host [R][14][nx_grid] (float64 for fp64, float32 otherwise)."""
+        dt = np.float64 if _prec(prec) == _lib.FK_FP64 else np.float32
+        F = np.ascontiguousarray(F, dtype=dt)
+        tk = ctypes.c_uint64()
+        _lib.call("fk_serve_submit", self._h, int(table_id), _p(F), F.shape[0], _prec(prec),
+                  ctypes.byref(tk))
+        self._meta[tk.value] = (F.shape[0], self._tables[table_id].ndata, dt)
+        return tk.value
+
+    def _out(self, ticket):
+        if ticket not in self._meta:  # let the library report the unknown ticket
+            return None
+        R, nd, dt = self._meta[ticket]
+        return np.empty((R, nd), dtype=dt)
+
+    def poll(self, ticket: int):
+        """(True, O) when done, (False, None) while pending; raises on failure."""
+        O = self._out(ticket)
+        done = ctypes.c_int()
+        rc = _lib.load().fk_serve_poll(self._h, ctypes.c_uint64(ticket), _p(O), ctypes.byref(done))
+        if rc == _lib.FK_EPENDING:
+            return False, None
+        self._meta.pop(ticket, None)
+        if rc != 0:
+            raise FKError("fk_serve_poll", rc, _lib.load())
+        return True, O
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> np.ndarray:
+        O = self._out(ticket)
+        rc = _lib.load().fk_serve_wait(self._h, ctypes.c_uint64(ticket), _p(O), int(timeout_ms))
+        if rc == _lib.FK_ETIMEDOUT:
+            raise TimeoutError(f"ticket {ticket} still running after {timeout_ms} ms")
+        self._meta.pop(ticket, None)
+        if rc != 0:
+            raise FKError("fk_serve_wait", rc, _lib.load())
+        return O
+
+    def stats(self) -> dict:
+        c, d, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        pk, q = ctypes.c_size_t(), ctypes.c_int()
+        _lib.call("fk_serve_stats", self._h, ctypes.byref(c), ctypes.byref(d), ctypes.byref(n),
+                  ctypes.byref(pk), ctypes.byref(q))
+        return dict(completed=c.value, datapoint_replicas=d.value, launches=n.value,
+                    peak_bytes=pk.value, queued=q.value)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.load().fk_serve_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FKConv(torch.autograd.Function):

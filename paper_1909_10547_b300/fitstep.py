@@ -32,6 +32,9 @@ class GlobalFit:
             st = store if hasattr(t, "ca") else tuple(p for p in store if p in ("fp64", "fp32")) or ("fp32",)
             self.tabs.append(Table.from_workload(t, st))
         self.kinds = ["had" if hasattr(t, "ca") else "dis" for t in tables]
+        # DIS tables are small linear contractions: in the reduced modes they
+        # run in FP32 on the CUDA cores (the tensor-core modes are hadronic)
+        self.tprec = [prec if (k == "had" or prec in ("fp64", "fp32")) else "fp32" for k in self.kinds]
         nd = [t.ndata for t in tables]
         self.offs = np.concatenate([[0], np.cumsum(nd)]).astype(int)
         self.ntot = int(self.offs[-1])
@@ -66,7 +69,7 @@ class GlobalFit:
     # -- phases ------------------------------------------------------------
     def forward(self):
         for k, t in enumerate(self.tabs):
-            conv(t, self.F, self.prec, out=self.O[:, self.offs[k]:self.offs[k + 1]])
+            conv(t, self.F, self.tprec[k], out=self.O[:, self.offs[k]:self.offs[k + 1]])
 
     def loss(self):
         chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)

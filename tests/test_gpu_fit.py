@@ -1,0 +1,137 @@
+"""Differentiable fit step: autograd wrapper, chi^2 gradient, finite differences.
+
+The fit of the paper is gradient descent (Sec. 2), so the adjoint must give
+dchi2/df_a(x_i).  Checks: (1) FKConv.backward equals the oracle gradient;
+(2) the fit step's gradient equals the oracle chain (oracle forward, oracle
+chi^2 gradient, oracle adjoint); (3) it matches central finite differences of
+the GPU chi^2 with h = 1e-6 (absolute, FP64) on sampled coordinates and random
+directions, to 1e-6 of max(|g.v|, 1e-3 |g|).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1909_10547_b300 as fk
+from paper_1909_10547_b300 import workloads as W
+from paper_1909_10547_b300.fitstep import GlobalFit
+
+pytestmark = pytest.mark.gpu
+
+SEED = 77
+
+
+@pytest.fixture(scope="module")
+def small_global():
+    g = W.config3(R=6, scale=0.12, seed=SEED)
+    o_true = [oracle.conv(t, g.F_true)[0][0] for t in g.tables]
+    cov = W.covariance(o_true, SEED)
+    D = W.pseudo_data(o_true, SEED)
+    return g, cov, D
+
+
+def oracle_chain(g, cov, D, F):
+    chi = np.zeros(F.shape[0])
+    gF = np.zeros_like(F)
+    for t, b, d in zip(g.tables, cov.blocks, D):
+        O, _ = oracle.conv(t, F)
+        L = oracle.cholesky(b)
+        c, gO = oracle.chi2(L, O, d)
+        chi += c
+        gF += oracle.conv_grad(t, F, gO)
+    return chi, gF
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autograd_matches_oracle_gradient(prec):
+    t, F = W.config1(R=5, ndata=40, nc=20, nx=16)
+    tab = fk.Table.from_workload(t)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Fd = torch.tensor(F, dtype=dt, device="cuda", requires_grad=True)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((5, t.ndata))
+    O = fk.FKConv.apply(Fd, tab, prec)
+    (O * torch.tensor(w, dtype=dt, device="cuda")).sum().backward()
+    ref = oracle.had_grad(t, F, w)
+    a = oracle.had_grad(W.HadTable(np.abs(t.fk), t.ca, t.cb, t.xmap, t.nxg), np.abs(F), np.abs(w))
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.all(np.abs(Fd.grad.double().cpu().numpy() - ref) <= tol * a)
+
+
+def test_fit_step_gradient_matches_oracle_chain(small_global):
+    g, cov, D = small_global
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp64")
+    fit.step()
+    torch.cuda.synchronize()
+    chi_ref, gF_ref = oracle_chain(g, cov, D, g.F)
+    chi = fit.chi2.cpu().numpy()
+    gF = fit.gF.cpu().numpy()
+    np.testing.assert_allclose(chi, chi_ref, rtol=1e-11)
+    scale = np.abs(gF_ref).max()
+    assert np.abs(gF - gF_ref).max() <= 1e-11 * scale
+
+
+def test_fit_step_gradient_finite_differences(small_global):
+    g, cov, D = small_global
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp64")
+    fit.step()
+    torch.cuda.synchronize()
+    grad = fit.gF.cpu().numpy().copy()
+    F0 = fit.F.clone()
+    h = 1e-6
+
+    def chi2_at(F):
+        fit.F.copy_(torch.tensor(F, device="cuda"))
+        fit.forward()
+        fit.loss()
+        torch.cuda.synchronize()
+        return fit.chi2.cpu().numpy().copy()
+
+    rng = np.random.default_rng(3)
+    gnorm = np.linalg.norm(grad)
+    used = set(int(m) for t in g.tables for m in t.xmap)
+    for n in range(24):
+        v = np.zeros_like(g.F)
+        if n < 16:  # single coordinates on grid points some table uses
+            r, a = int(rng.integers(g.F.shape[0])), int(rng.integers(14))
+            m = int(rng.choice(sorted(used)))
+            v[r, a, m] = 1.0
+        else:       # random unit directions
+            v = rng.standard_normal(g.F.shape)
+            v /= np.linalg.norm(v)
+        fd = (chi2_at(g.F + h * v) - chi2_at(g.F - h * v)) / (2 * h)
+        gv = (grad * v).sum(axis=(1, 2))
+        for r in range(g.F.shape[0]):
+            assert abs(fd[r] - gv[r]) <= 1e-6 * max(abs(gv[r]), 1e-3 * gnorm), (n, r, fd[r], gv[r])
+    fit.F.copy_(F0)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-3), ("tf32", 5e-2), ("bf16", 0.5)])
+def test_fit_step_reduced_precision_chi2(small_global, prec, tol):
+    """chi^2 of the reduced-precision fit step against the FP64 oracle; the
+    stated error of each mode is a relative bound on chi^2 here."""
+    g, cov, D = small_global
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec=prec)
+    fit.step()
+    torch.cuda.synchronize()
+    chi_ref, gF_ref = oracle_chain(g, cov, D, g.F)
+    chi = fit.chi2.cpu().numpy()
+    rel = np.abs(chi - chi_ref) / np.abs(chi_ref)
+    print(prec, "chi2 rel err", rel.max())
+    assert rel.max() <= tol
+
+
+def test_graph_capture_replays_the_step(small_global):
+    g, cov, D = small_global
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp32")
+    fit.step()
+    torch.cuda.synchronize()
+    chi_eager = fit.chi2.cpu().numpy().copy()
+    gF_eager = fit.gF.cpu().numpy().copy()
+    fit.capture()
+    fit.chi2.zero_()
+    fit.gF.zero_()
+    fit.step()
+    torch.cuda.synchronize()
+    assert np.array_equal(fit.chi2.cpu().numpy(), chi_eager)
+    assert np.array_equal(fit.gF.cpu().numpy(), gF_eager)

@@ -184,8 +184,11 @@ int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ld
  * otherwise).  accumulate = 0 overwrites all of gF (grid points the table does
  * not use are set to 0); accumulate = 1 adds into gF, so the gradients of
  * several tables sharing one grid can be summed in call order.  F is not read
- * for DIS tables (may be NULL).  Reduced modes compute in FP32 on the CUDA
- * cores and need the table's FP32 copy (FK_EUNSUPPORTED otherwise).
+ * for DIS tables (may be NULL).  The reduced modes (hadronic tables) run on
+ * the tensor cores with the forward's operand rounding: the products of the
+ * table with the PDF of one flavour go through the MMA in the mode's type with
+ * FP32 accumulation, and gO and the remaining PDF factor are applied in FP32.
+ * Like the forward, they are offered for hadronic tables only.
  */
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
                      void *gF, int accumulate, int prec, fk_stream stream);

@@ -262,10 +262,11 @@ int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo,
     if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
     if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
     const bool f64 = prec == FK_FP64;
-    if (!f64 && !t->fk32)
-        return fail(FK_EUNSUPPORTED, "the adjoint in reduced modes needs the table's FP32 copy");
-    return bwd_cc(t, F, gO, ldgo ? ldgo : t->ndata, R, gF, accumulate ? 1 : 0, f64,
-                  (cudaStream_t)stream);
+    ldgo = ldgo ? ldgo : t->ndata;
+    if (prec != FK_FP64 && prec != FK_FP32)  // tensor-core modes (hadronic tables only)
+        return bwd_tc(t, (const float *)F, (const float *)gO, ldgo, R, (float *)gF, accumulate ? 1 : 0,
+                      prec, (cudaStream_t)stream);
+    return bwd_cc(t, F, gO, ldgo, R, gF, accumulate ? 1 : 0, f64, (cudaStream_t)stream);
 }
 
 }  // extern "C"

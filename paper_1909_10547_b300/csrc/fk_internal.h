@@ -62,18 +62,29 @@ struct TcGroups {
     int chan[MAX_CH]; // channel ids ordered by group
 };
 
-// Tensor-core layout of a hadronic table: the B operand of the MMA, one tile
-// of n_rows rows per G data points, K-major with row length ktot_pad.
-struct TcLayout {
+// One packing of a hadronic table as the B operand of the MMA: one tile of
+// n_rows rows per G data points, K-major with row length ktot_pad.
+//  - forward packing: groups by the first flavour a_c; row n = i * G + d % G
+//    holds x_i, K runs over (channel, x_j);
+//  - transposed packing (adjoint): groups by the second flavour b_c; row
+//    n = j * G + d % G holds x_j, K runs over (channel, x_i).
+struct TcPack {
     TcGroups grp{};
-    int G = 0;          // data points per tile (power of two, G * nx <= 256)
-    int ntile_n = 0;    // ceil(ndata / G)
-    int n_rows = 0;     // MMA N = G * nx rounded up to 16; row n = i * G + (d % G)
     int ktot = 0;       // used K (sum of padded group lengths)
     int ktot_pad = 0;   // row length, a multiple of 64
-    CUtensorMap map_hi;   // BF16 / hi part (the type is 128-byte aligned)
-    CUtensorMap map_lo;   // lo part
-    CUtensorMap map_f32;  // TF32 operand
+    __nv_bfloat16 *hi = nullptr;  // BF16 / hi part
+    __nv_bfloat16 *lo = nullptr;  // lo part (BF16X3)
+    float *f32 = nullptr;         // TF32 operand (FP32 bits, rounded)
+    CUtensorMap map_hi;   // (the type is 128-byte aligned)
+    CUtensorMap map_lo;
+    CUtensorMap map_f32;
+};
+
+struct TcLayout {
+    int G = 0;          // data points per tile (power of two, G * nx <= 256)
+    int ntile_n = 0;    // ceil(ndata / G)
+    int n_rows = 0;     // MMA N = G * nx rounded up to 16
+    TcPack fwd, bwd;
 };
 
 }  // namespace fk
@@ -94,9 +105,6 @@ struct fk_table {
     float *fk32 = nullptr;          // [ndata][ldE]
     // tensor-core layouts (hadronic): packed B operand tiles
     fk::TcLayout tc;
-    __nv_bfloat16 *tc_hi = nullptr; // BF16 (or hi part)
-    __nv_bfloat16 *tc_lo = nullptr; // lo part (BF16X3)
-    float *tc_f32 = nullptr;        // TF32 operand (FP32 bits)
     size_t bytes = 0;
 };
 
@@ -120,6 +128,8 @@ int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, vo
 // tensor-core path (k_tc.cu)
 int tc_build(fk_table *t, const double *host_fk);
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
+int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
+           int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);
 // FK_ETIMEDOUT if a kernel's bounded wait ran out since the last reset
 int device_status(int reset);

@@ -169,9 +169,17 @@ struct Tr {
 struct TcParams {
     int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
     int kbeg[NFL], kend[NFL];
-    const float *Fm;  // [ngroups][nx][R_pad] epilogue multipliers f^r_{a_g}(x_i)
-    float *O;
+    const float *Fm;  // forward: [ngroups][nx][R_pad] epilogue multipliers f^r_{a_g}(x_i)
+    float *O;         // forward: observables, row stride ldo
+    const float *gO;  // adjoint: weights gO[r * ldo + d]
+    float *P;         // adjoint: partial sums [ntile_n][ngroups][nx][R_pad]
 };
+
+// Epilogue modes of the tensor-core kernel.
+//  FWD: O[r][d]   = sum_g sum_i f^r_{a_g}(x_i) Y_g[r][(i, d)]
+//  ADJ: P[t][g][i][r] = sum_{d in tile t} gO[r][d] Y_g[r][(i, d)]
+// (with the transposed packing, i stands for x_j and g for the second flavour)
+enum { MODE_FWD = 0, MODE_ADJ = 1 };
 
 template <int PREC>
 size_t tc_smem_bytes(int n_rows) {
@@ -179,7 +187,7 @@ size_t tc_smem_bytes(int n_rows) {
     return 1024 + Tr<PREC>::STAGES * stage + 256;
 }
 
-template <int PREC, int G>
+template <int PREC, int G, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
          const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
@@ -337,16 +345,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float acc[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) acc[u] = 0.f;
+            // adjoint: this replica's weights for the tile's G data points
+            if (MODE == MODE_ADJ) {
+#pragma unroll
+                for (int dl = 0; dl < G; ++dl) {
+                    const int dd = nt * G + dl;
+                    acc[dl] = (r < p.R && dd < p.ndata) ? __ldg(p.gO + (size_t)r * p.ldo + dd) : 0.f;
+                }
+            }
             const int ncols = ((G * p.nx + 31) / 32) * 32;
             constexpr int MI = 256 / G;  // x points a 256-column accumulator can hold
             for (int g = 0; g < p.ngroups; ++g, ++gc) {
                 const int b = gc & 1;
                 // the multipliers f^r_{a_g}(x_i) do not depend on the MMA:
                 // fetch them all before waiting so their latency overlaps it
-                const float *fm = p.Fm + (size_t)g * p.nx * p.R_pad + r;
-                float m[MI];
+                float m[MODE == MODE_FWD ? MI : 1];
+                if (MODE == MODE_FWD) {
+                    const float *fm = p.Fm + (size_t)g * p.nx * p.R_pad + r;
 #pragma unroll
-                for (int i = 0; i < MI; ++i) m[i] = i < p.nx ? __ldg(fm + (size_t)i * p.R_pad) : 0.f;
+                    for (int i = 0; i < MI; ++i) m[i] = i < p.nx ? __ldg(fm + (size_t)i * p.R_pad) : 0.f;
+                }
                 // one lane waits, the warp follows (tcgen05.ld is warp-collective)
                 int got = 1;
                 if (lane == 0) got = mbar_wait(accf(b), (gc >> 1) & 1, dead);
@@ -357,16 +375,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+                float *pg = MODE == MODE_ADJ ? p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r : nullptr;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     if (c * 32 < ncols) {
                         uint32_t v[32];
                         tmem_ld32(taddr + (uint32_t)(c * 32), v);
+                        if (MODE == MODE_FWD) {
 #pragma unroll
-                        for (int u = 0; u < 32 / G; ++u)
+                            for (int u = 0; u < 32 / G; ++u)
 #pragma unroll
-                            for (int dl = 0; dl < G; ++dl)
-                                acc[dl] = fmaf(m[c * (32 / G) + u], __uint_as_float(v[u * G + dl]), acc[dl]);
+                                for (int dl = 0; dl < G; ++dl)
+                                    acc[dl] = fmaf(m[c * (32 / G) + u], __uint_as_float(v[u * G + dl]), acc[dl]);
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 32 / G; ++u) {
+                                const int i = c * (32 / G) + u;
+                                float s = 0.f;
+#pragma unroll
+                                for (int dl = 0; dl < G; ++dl) s = fmaf(acc[dl], __uint_as_float(v[u * G + dl]), s);
+                                if (i < p.nx) pg[(size_t)i * p.R_pad] = s;
+                            }
+                        }
                     }
                 }
                 tc_fence_before();
@@ -374,7 +404,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(acce(b));
             }
             if (!ok) break;
-            if (r < p.R) {
+            if (MODE == MODE_FWD && r < p.R) {
 #pragma unroll
                 for (int dl = 0; dl < G; ++dl) {
                     const int dd = nt * G + dl;
@@ -416,14 +446,16 @@ __device__ __forceinline__ int group_of(const TcGroups &gr, int k) {
     return -1;
 }
 
-// A operand A[r][k] = f^r_{b_c}(x_j) for k = (channel c of its group, j), and
-// the epilogue multipliers Fm[g][i][r] = f^r_{a_g}(x_i).
+// A operand A[r][k] = f^r_{o_c}(x_j) for k = (channel c of its group, j), where
+// o_c is the channel's other flavour (b_c for the forward packing, a_c for the
+// transposed one), and, if Fm is not NULL, the forward epilogue multipliers
+// Fm[g][i][r] = f^r_{a_g}(x_i).
 template <int PREC>
 __global__ void k_pack_pdf(const TcGroups gr, const int *__restrict__ cb, const int *__restrict__ xmap,
                            int nx, int nxg, const float *__restrict__ F, int R, int R_pad, int ktot_pad,
                            __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32, float *__restrict__ Fm) {
     const long long nA = (long long)R_pad * ktot_pad;
-    const long long nM = (long long)gr.ngroups * nx * R_pad;
+    const long long nM = Fm ? (long long)gr.ngroups * nx * R_pad : 0;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nA + nM;
          idx += (long long)gridDim.x * blockDim.x) {
         if (idx < nA) {
@@ -448,11 +480,13 @@ __global__ void k_pack_pdf(const TcGroups gr, const int *__restrict__ cb, const 
     }
 }
 
-// B operand from the FP64 table [ndata][nc][nx][nx]: row nt * n_rows + i * G + dl
-// holds data point d = nt * G + dl at x_i; column k = (channel of its group, x_j).
+// B operand from the FP64 table [ndata][nc][nx][nx]: row nt * n_rows + u * G + dl
+// holds data point d = nt * G + dl at the row's x point u; column k = (channel
+// of its group, x point v).  Forward packing: (u, v) = (i, j); transposed
+// packing (trans = 1): (u, v) = (j, i).
 template <int PREC>
 __global__ void k_pack_table(const TcGroups gr, const double *__restrict__ fk, int ndata, int nc,
-                             int nx, int G, int n_rows, int ntile_n, int ktot_pad,
+                             int nx, int G, int n_rows, int ntile_n, int ktot_pad, int trans,
                              __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
     const long long n = (long long)ntile_n * n_rows * ktot_pad;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
@@ -468,11 +502,36 @@ __global__ void k_pack_table(const TcGroups gr, const double *__restrict__ fk, i
             const int q = (k - gr.kbeg[g]) / nx, j = (k - gr.kbeg[g]) % nx;
             if (q < gr.nch[g]) {
                 const int c = gr.chan[gr.ch0[g] + q];
-                v = (float)fk[(((size_t)d * nc + c) * nx + i) * nx + j];
+                const int xi = trans ? j : i, xj = trans ? i : j;
+                v = (float)fk[(((size_t)d * nc + c) * nx + xi) * nx + xj];
             }
         }
         store_op<PREC>(idx, v, hi, lo, f32);
     }
+}
+
+// Adjoint gather: gF[r][a][m] (+)= sum_t P1[t][g1(a)][i(m)][r] + sum_t P2[t][g2(a)][i(m)][r]
+// with i(m) the table's x index of grid point m, g1/g2 the groups of flavour a
+// in the forward and transposed packings (-1: none); tiles t in order.
+__global__ void k_adj_gather(const float *__restrict__ P1, const float *__restrict__ P2, int ntile,
+                             int ng1, int ng2, const int8_t *__restrict__ g1, const int8_t *__restrict__ g2,
+                             const int *__restrict__ xinv, int nx, int nxg, int R, int R_pad,
+                             int accumulate, float *__restrict__ gF) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * NFL * nxg) return;
+    const int r = (int)(idx % R);
+    const int m = (int)((idx / R) % nxg);
+    const int a = (int)(idx / ((long long)R * nxg));
+    const int i = xinv[m];
+    float s = 0.f;
+    if (i >= 0) {
+        if (g1[a] >= 0)
+            for (int t = 0; t < ntile; ++t) s += P1[(((size_t)t * ng1 + g1[a]) * nx + i) * R_pad + r];
+        if (g2[a] >= 0)
+            for (int t = 0; t < ntile; ++t) s += P2[(((size_t)t * ng2 + g2[a]) * nx + i) * R_pad + r];
+    }
+    const size_t o = ((size_t)r * NFL + a) * nxg + m;
+    gF[o] = accumulate ? gF[o] + s : s;
 }
 
 // ------------------------------------------------------------ host ----
@@ -525,18 +584,78 @@ int opt_in_smem(K kernel, size_t bytes) {
     return FK_OK;
 }
 
-template <int PREC, int G>
+template <int PREC, int G, int MODE>
 int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
               const CUtensorMap &mB2, const TcParams &p, cudaStream_t s) {
     const size_t smem = tc_smem_bytes<PREC>(t->tc.n_rows);
     // opt in once at the largest tile (n_rows = 256) so that every table fits
-    int rc = opt_in_smem(k_tc<PREC, G>, tc_smem_bytes<PREC>(256));
+    int rc = opt_in_smem(k_tc<PREC, G, MODE>, tc_smem_bytes<PREC>(256));
     if (rc) return rc;
     const int grid = std::min(p.ntiles, sm_count());
-    k_tc<PREC, G><<<grid, TC_THREADS, smem, s>>>(mA, mA2, mB, mB2, p);
+    k_tc<PREC, G, MODE><<<grid, TC_THREADS, smem, s>>>(mA, mA2, mB, mB2, p);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
+}
+
+template <int PREC, int MODE>
+int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
+                const CUtensorMap &mB2, const TcParams &p, cudaStream_t s) {
+    switch (t->tc.G) {
+        case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mB, mB2, p, s);
+        case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mB, mB2, p, s);
+        case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mB, mB2, p, s);
+    }
+    return fail(FK_EINVAL, "bad tile height");
+}
+
+// Packs the A operand (and, if Fm is not NULL, the forward multipliers) for one
+// packing of the table, builds its tensor maps and fills the common params.
+template <int PREC>
+int prepare(const fk_table *t, const TcPack &pk, const int *d_other, const float *F, int R, Scratch &scr,
+            float *Fm, cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p) {
+    const TcLayout &L = t->tc;
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    float *f32 = nullptr;
+    const size_t nA = (size_t)R_pad * pk.ktot_pad;
+    if (PREC == FK_TF32) {
+        FK_CUDA(scr.get(&f32, nA));
+    } else {
+        FK_CUDA(scr.get(&hi, nA));
+        if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
+    }
+    const long long n = (long long)nA + (Fm ? (long long)pk.grp.ngroups * t->nx * R_pad : 0);
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 8);
+    k_pack_pdf<PREC><<<blocks, 256, 0, s>>>(pk.grp, d_other, t->d_xmap, t->nx, t->nxg, F, R, R_pad,
+                                            pk.ktot_pad, hi, lo, f32, Fm);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    const int esz = Tr<PREC>::ESZ;
+    int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
+    if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);
+    if (rc) return rc;
+    if (PREC != FK_BF16X3) mA2 = mA;
+    p = TcParams{};
+    p.nrt = R_pad / TC_M;
+    p.ntiles = L.ntile_n * p.nrt;
+    p.nchunks = pk.ktot_pad / Tr<PREC>::KC;
+    p.n_rows = L.n_rows;
+    p.ngroups = pk.grp.ngroups;
+    p.nx = t->nx;
+    p.ndata = t->ndata;
+    p.R = R;
+    p.R_pad = R_pad;
+    for (int g = 0; g < pk.grp.ngroups; ++g) {
+        p.kbeg[g] = pk.grp.kbeg[g];
+        p.kend[g] = pk.grp.kend[g];
+    }
+    return FK_OK;
+}
+
+const CUtensorMap &map_b(const TcPack &pk, int prec, bool second) {
+    if (prec == FK_TF32) return pk.map_f32;
+    return (second && prec == FK_BF16X3) ? pk.map_lo : pk.map_hi;
 }
 
 template <int PREC>
@@ -544,81 +663,84 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     const TcLayout &L = t->tc;
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     Scratch scr(s);
-    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
-    float *f32 = nullptr, *Fm = nullptr;
-    const size_t nA = (size_t)R_pad * L.ktot_pad;
-    if (PREC == FK_TF32) {
-        FK_CUDA(scr.get(&f32, nA));
-    } else {
-        FK_CUDA(scr.get(&hi, nA));
-        if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
-    }
-    FK_CUDA(scr.get(&Fm, (size_t)L.grp.ngroups * t->nx * R_pad));
-    {
-        const long long n = (long long)nA + (long long)L.grp.ngroups * t->nx * R_pad;
-        const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 8);
-        k_pack_pdf<PREC><<<blocks, 256, 0, s>>>(L.grp, t->d_cb, t->d_xmap, t->nx, t->nxg, F, R, R_pad,
-                                                L.ktot_pad, hi, lo, f32, Fm);
-        count_launch();
-        FK_CUDA(cudaGetLastError());
-    }
+    float *Fm = nullptr;
+    FK_CUDA(scr.get(&Fm, (size_t)L.fwd.grp.ngroups * t->nx * R_pad));
     CUtensorMap mA, mA2;
-    const int esz = Tr<PREC>::ESZ;
-    int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, L.ktot_pad, R_pad, TC_M);
-    if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, L.ktot_pad, R_pad, TC_M);
+    TcParams p;
+    int rc = prepare<PREC>(t, L.fwd, t->d_cb, F, R, scr, Fm, s, mA, mA2, p);
     if (rc) return rc;
-    if (PREC != FK_BF16X3) mA2 = mA;
-    const CUtensorMap &mB = PREC == FK_TF32 ? L.map_f32 : L.map_hi;
-    const CUtensorMap &mB2 = PREC == FK_BF16X3 ? L.map_lo : mB;
-
-    TcParams p{};
-    p.nrt = R_pad / TC_M;
-    p.ntiles = L.ntile_n * p.nrt;
-    p.nchunks = L.ktot_pad / Tr<PREC>::KC;
-    p.n_rows = L.n_rows;
-    p.ngroups = L.grp.ngroups;
-    p.nx = t->nx;
-    p.ndata = t->ndata;
-    p.R = R;
-    p.R_pad = R_pad;
     p.ldo = ldo;
-    for (int g = 0; g < L.grp.ngroups; ++g) {
-        p.kbeg[g] = L.grp.kbeg[g];
-        p.kend[g] = L.grp.kend[g];
-    }
     p.Fm = Fm;
     p.O = O;
-    switch (L.G) {
-        case 4: return launch_tc<PREC, 4>(t, mA, mA2, mB, mB2, p, s);
-        case 8: return launch_tc<PREC, 8>(t, mA, mA2, mB, mB2, p, s);
-        case 16: return launch_tc<PREC, 16>(t, mA, mA2, mB, mB2, p, s);
-    }
-    return fail(FK_EINVAL, "bad tile height");
+    return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, map_b(L.fwd, PREC, false), map_b(L.fwd, PREC, true), p, s);
 }
 
+// Adjoint: term 1 (derivative with respect to the first flavour of each
+// channel) from the forward packing, term 2 (second flavour) from the
+// transposed packing, both as per-tile partial sums, then one fixed-order
+// gather into gF.
 template <int PREC>
-int pack_table(fk_table *t, const double *d_fk, cudaStream_t s) {
+int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
+             int accumulate, cudaStream_t s) {
     const TcLayout &L = t->tc;
-    const long long n = (long long)L.ntile_n * L.n_rows * L.ktot_pad;
-    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 32);
-    k_pack_table<PREC><<<blocks, 256, 0, s>>>(L.grp, d_fk, t->ndata, t->nch, t->nx, L.G, L.n_rows,
-                                              L.ntile_n, L.ktot_pad, t->tc_hi, t->tc_lo, t->tc_f32);
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    Scratch scr(s);
+    float *P1 = nullptr, *P2 = nullptr;
+    int8_t *gmap = nullptr;
+    FK_CUDA(scr.get(&P1, (size_t)L.ntile_n * L.fwd.grp.ngroups * t->nx * R_pad));
+    FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
+    FK_CUDA(scr.get(&gmap, 2 * NFL));
+    int8_t hmap[2 * NFL];
+    for (int a = 0; a < 2 * NFL; ++a) hmap[a] = -1;
+    for (int g = 0; g < L.fwd.grp.ngroups; ++g) hmap[L.fwd.grp.flav[g]] = (int8_t)g;
+    for (int g = 0; g < L.bwd.grp.ngroups; ++g) hmap[NFL + L.bwd.grp.flav[g]] = (int8_t)g;
+    FK_CUDA(cudaMemcpyAsync(gmap, hmap, sizeof(hmap), cudaMemcpyHostToDevice, s));
+    const TcPack *packs[2] = {&L.fwd, &L.bwd};
+    const int *others[2] = {t->d_cb, t->d_ca};
+    float *parts[2] = {P1, P2};
+    for (int k = 0; k < 2; ++k) {
+        CUtensorMap mA, mA2;
+        TcParams p;
+        int rc = prepare<PREC>(t, *packs[k], others[k], F, R, scr, nullptr, s, mA, mA2, p);
+        if (rc) return rc;
+        p.ldo = ldgo;
+        p.gO = gO;
+        p.P = parts[k];
+        rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, map_b(*packs[k], PREC, false), map_b(*packs[k], PREC, true),
+                                         p, s);
+        if (rc) return rc;
+    }
+    const long long n = (long long)R * NFL * t->nxg;
+    k_adj_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P1, P2, L.ntile_n, L.fwd.grp.ngroups,
+                                                             L.bwd.grp.ngroups, gmap, gmap + NFL, t->d_xinv,
+                                                             t->nx, t->nxg, R, R_pad, accumulate, gF);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
 }
 
-}  // namespace
+template <int PREC>
+int pack_table(fk_table *t, TcPack &pk, int trans, const double *d_fk, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const long long n = (long long)L.ntile_n * L.n_rows * pk.ktot_pad;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 32);
+    k_pack_table<PREC><<<blocks, 256, 0, s>>>(pk.grp, d_fk, t->ndata, t->nch, t->nx, L.G, L.n_rows,
+                                              L.ntile_n, pk.ktot_pad, trans, pk.hi, pk.lo, pk.f32);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
 
-int tc_build(fk_table *t, const double *host_fk) {
-    TcLayout &L = t->tc;
-    TcGroups &gr = L.grp;
+// Channel groups keyed by `key` (the first flavour for the forward packing,
+// the second for the transposed one), each padded to KPAD along K.
+void make_groups(const fk_table *t, const std::vector<int> &key, TcPack &pk) {
+    TcGroups &gr = pk.grp;
     gr.ngroups = 0;
     int k = 0, pos = 0;
     for (int a = 0; a < NFL; ++a) {
         int n = 0;
         for (int c = 0; c < t->nch; ++c)
-            if (t->ca[c] == a) {
+            if (key[c] == a) {
                 if (!n) {
                     gr.flav[gr.ngroups] = a;
                     gr.ch0[gr.ngroups] = pos;
@@ -634,22 +756,31 @@ int tc_build(fk_table *t, const double *host_fk) {
             ++gr.ngroups;
         }
     }
-    L.ktot = k;
-    L.ktot_pad = (k + 63) / 64 * 64;
+    pk.ktot = k;
+    pk.ktot_pad = (k + 63) / 64 * 64;
+}
+
+}  // namespace
+
+int tc_build(fk_table *t, const double *host_fk) {
+    TcLayout &L = t->tc;
+    make_groups(t, t->ca, L.fwd);
+    make_groups(t, t->cb, L.bwd);
     L.G = t->nx <= 16 ? 16 : (t->nx <= 32 ? 8 : 4);
     L.n_rows = (L.G * t->nx + 15) / 16 * 16;
     L.ntile_n = (t->ndata + L.G - 1) / L.G;
-    const size_t elems = (size_t)L.ntile_n * L.n_rows * L.ktot_pad;
     const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
     const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
     const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
-    if ((want_hi && cudaMalloc(&t->tc_hi, elems * 2)) || (want_lo && cudaMalloc(&t->tc_lo, elems * 2)) ||
-        (want_f32 && cudaMalloc(&t->tc_f32, elems * 4)))
-        return fail(FK_ENOMEM, "tensor-core table storage");
-    t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+    for (TcPack *pk : {&L.fwd, &L.bwd}) {
+        const size_t elems = (size_t)L.ntile_n * L.n_rows * pk->ktot_pad;
+        if ((want_hi && cudaMalloc(&pk->hi, elems * 2)) || (want_lo && cudaMalloc(&pk->lo, elems * 2)) ||
+            (want_f32 && cudaMalloc(&pk->f32, elems * 4)))
+            return fail(FK_ENOMEM, "tensor-core table storage");
+        t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+    }
 
     // full FP64 copy on the device for the packing kernels, then freed
-    const double *d_src = nullptr;
     double *owned = nullptr;
     cudaStream_t s = nullptr;
     FK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -659,12 +790,14 @@ int tc_build(fk_table *t, const double *host_fk) {
         cudaStreamDestroy(s);
         return fail(FK_ENOMEM, "tensor-core packing staging");
     }
-    d_src = owned;
     cudaError_t e = cudaMemcpyAsync(owned, host_fk, src_elems * 8, cudaMemcpyHostToDevice, s);
     if (e) rc = cuda_fail(e, "tensor-core table upload");
-    if (!rc && want_f32) rc = pack_table<FK_TF32>(t, d_src, s);
-    if (!rc && want_lo) rc = pack_table<FK_BF16X3>(t, d_src, s);
-    else if (!rc && want_hi) rc = pack_table<FK_BF16>(t, d_src, s);
+    for (int tr = 0; tr < 2 && !rc; ++tr) {
+        TcPack &pk = tr ? L.bwd : L.fwd;
+        if (!rc && want_f32) rc = pack_table<FK_TF32>(t, pk, tr, owned, s);
+        if (!rc && want_lo) rc = pack_table<FK_BF16X3>(t, pk, tr, owned, s);
+        else if (!rc && want_hi) rc = pack_table<FK_BF16>(t, pk, tr, owned, s);
+    }
     if (!rc) {
         e = cudaStreamSynchronize(s);
         if (e) rc = cuda_fail(e, "tensor-core table packing");
@@ -673,9 +806,11 @@ int tc_build(fk_table *t, const double *host_fk) {
     cudaStreamDestroy(s);
     if (rc) return rc;
     const long long rows = (long long)L.ntile_n * L.n_rows;
-    if (want_hi && (rc = make_map(&L.map_hi, t->tc_hi, 2, L.ktot_pad, rows, L.n_rows))) return rc;
-    if (want_lo && (rc = make_map(&L.map_lo, t->tc_lo, 2, L.ktot_pad, rows, L.n_rows))) return rc;
-    if (want_f32 && (rc = make_map(&L.map_f32, t->tc_f32, 4, L.ktot_pad, rows, L.n_rows))) return rc;
+    for (TcPack *pk : {&L.fwd, &L.bwd}) {
+        if (want_hi && (rc = make_map(&pk->map_hi, pk->hi, 2, pk->ktot_pad, rows, L.n_rows))) return rc;
+        if (want_lo && (rc = make_map(&pk->map_lo, pk->lo, 2, pk->ktot_pad, rows, L.n_rows))) return rc;
+        if (want_f32 && (rc = make_map(&pk->map_f32, pk->f32, 4, pk->ktot_pad, rows, L.n_rows))) return rc;
+    }
     return FK_OK;
 }
 
@@ -689,12 +824,25 @@ int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec
     return fail(FK_EINVAL, "not a tensor-core precision");
 }
 
+int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF, int accumulate,
+           int prec, cudaStream_t s) {
+    if (t->kind != FK_KIND_HAD) return fail(FK_EUNSUPPORTED, "tensor-core modes need a hadronic table");
+    switch (prec) {
+        case FK_BF16: return bwd_tc_t<FK_BF16>(t, F, gO, ldgo, R, gF, accumulate, s);
+        case FK_BF16X3: return bwd_tc_t<FK_BF16X3>(t, F, gO, ldgo, R, gF, accumulate, s);
+        case FK_TF32: return bwd_tc_t<FK_TF32>(t, F, gO, ldgo, R, gF, accumulate, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
+}
+
 void tc_free(fk_table *t) {
-    cudaFree(t->tc_hi);
-    cudaFree(t->tc_lo);
-    cudaFree(t->tc_f32);
-    t->tc_hi = t->tc_lo = nullptr;
-    t->tc_f32 = nullptr;
+    for (fk::TcPack *pk : {&t->tc.fwd, &t->tc.bwd}) {
+        cudaFree(pk->hi);
+        cudaFree(pk->lo);
+        cudaFree(pk->f32);
+        pk->hi = pk->lo = nullptr;
+        pk->f32 = nullptr;
+    }
 }
 
 int device_status(int reset) {

@@ -98,8 +98,8 @@ size_t request_device_bytes(const fk_table *t, int R, int prec) {
         b += esz * (size_t)R * t->ndata * 256;  // partial sums (the split is at most 196)
     } else {
         const size_t rpad = (size_t)(R + 127) / 128 * 128;
-        b += rpad * t->tc.ktot_pad * (prec == FK_TF32 ? 4 : (prec == FK_BF16X3 ? 4 : 2)) +
-             4 * rpad * (size_t)t->tc.grp.ngroups * t->nx;
+        b += rpad * t->tc.fwd.ktot_pad * (prec == FK_TF32 ? 4 : (prec == FK_BF16X3 ? 4 : 2)) +
+             4 * rpad * (size_t)t->tc.fwd.grp.ngroups * t->nx;
     }
     return b + 4096;
 }

@@ -26,7 +26,7 @@ class GlobalFit:
         self.prec = prec
         io = torch.float64 if prec == "fp64" else torch.float32
         if store is None:
-            store = ("fp64", "fp32") if prec in ("fp64", "fp32") else ("fp32", prec)
+            store = ("fp64", "fp32") if prec in ("fp64", "fp32") else (prec,)
         self.tabs = []
         for t in tables:
             st = store if hasattr(t, "ca") else tuple(p for p in store if p in ("fp64", "fp32")) or ("fp32",)
@@ -75,9 +75,8 @@ class GlobalFit:
         chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)
 
     def backward(self):
-        bprec = self.prec if self.prec in ("fp64", "fp32") else "fp32"
         for k, t in enumerate(self.tabs):
-            conv_backward(t, self.F, self.gO[:, self.offs[k]:self.offs[k + 1]], bprec,
+            conv_backward(t, self.F, self.gO[:, self.offs[k]:self.offs[k + 1]], self.tprec[k],
                           gF=self.gF, accumulate=k > 0)
 
     def step(self):

@@ -135,3 +135,20 @@ def test_graph_capture_replays_the_step(small_global):
     torch.cuda.synchronize()
     assert np.array_equal(fit.chi2.cpu().numpy(), chi_eager)
     assert np.array_equal(fit.gF.cpu().numpy(), gF_eager)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 2e-4), ("tf32", 2e-2), ("bf16", 0.15)])
+def test_fit_step_reduced_precision_gradient(small_global, prec, tol):
+    """dchi2/dF of the tensor-core fit step against the FP64 oracle chain,
+    relative to the largest gradient entry.  chi^2 weighs the residual O - D,
+    a few per cent of O, by C^-1, so an operand rounding of O is amplified in
+    the gradient: plain BF16 (measured ~6e-2) is too coarse to fit with, the
+    split BF16 operands (~8e-5) are not."""
+    g, cov, D = small_global
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec=prec)
+    fit.step()
+    torch.cuda.synchronize()
+    _, gF_ref = oracle_chain(g, cov, D, g.F)
+    err = np.abs(fit.gF.double().cpu().numpy() - gF_ref).max() / np.abs(gF_ref).max()
+    print(prec, "gradient rel err", err)
+    assert err <= tol

@@ -117,3 +117,66 @@ def test_tc_shared_grid_and_ldo():
         assert (np.abs(got[:, off:off + t.ndata] - O_ref) / S).max() <= BOUND["bf16x3"]
         off += t.ndata
     assert np.isnan(got[:, ntot:]).all()
+
+
+# ------------------------------------------------------------ adjoint ----
+
+def _grad_scale(t, F, gO):
+    a = W.HadTable(np.abs(t.fk), t.ca, t.cb, t.xmap, t.nxg)
+    return oracle.had_grad(a, np.abs(F), np.abs(gO))
+
+
+def run_bwd(tab, F, gO, prec, gF=None, accumulate=False):
+    out = fk.conv_backward(tab, torch.tensor(F, dtype=torch.float32, device="cuda"),
+                           torch.tensor(gO, dtype=torch.float32, device="cuda"), prec,
+                           gF=gF, accumulate=accumulate)
+    torch.cuda.synchronize()
+    assert fk._lib.load().fk_device_status(1) == 0
+    return out.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("shape", [(5, 6, 5, 9, 3), (37, 20, 17, 20, 130), (13, 3, 33, 40, 129),
+                                   (4, 11, 64, 64, 2), (1, 1, 1, 1, 1), (9, 196, 3, 3, 5)])
+def test_tc_adjoint_exact_small_integers(prec, shape):
+    nd, nc, nx, nxg, R = shape
+    t, F = int_table(sum(shape) + 1, nd, nc, nx, nxg, R)
+    gO = np.random.default_rng(9).integers(-3, 4, (R, nd)).astype(np.float64)
+    ref = oracle.had_grad(t, F, gO)
+    tab = fk.Table.from_workload(t, precs=(prec,))
+    assert np.array_equal(run_bwd(tab, F, gO, prec), ref)
+
+
+@pytest.mark.parametrize("prec", TC)
+@pytest.mark.parametrize("shape", [(200, 60, 30, 100), (129, 13, 50, 7), (33, 196, 8, 200), (7, 2, 17, 1)])
+def test_tc_adjoint_accuracy(prec, shape):
+    nd, nc, nx, R = shape
+    rng = np.random.default_rng(sum(shape))
+    x = W.xgrid(nx, 1e-6)
+    t = W.had_table(rng, nd, nc, x)
+    F = W.pdf_replicas(x, W.pdf_params(rng), R, rng)
+    gO = rng.standard_normal((R, nd))
+    ref = oracle.had_grad(t, F, gO)
+    S = _grad_scale(t, F, gO)
+    tab = fk.Table.from_workload(t, precs=(prec,))
+    got = run_bwd(tab, F, gO, prec)
+    err = (np.abs(got - ref) / np.maximum(S, 1e-300)).max()
+    print(prec, shape, "adjoint max err/S", err)
+    assert err <= BOUND[prec]
+
+
+def test_tc_adjoint_accumulates():
+    g = W.config3(R=9, scale=0.05)
+    had = [t for t in g.tables if hasattr(t, "ca")][:4]
+    gF = torch.zeros(g.F.shape, dtype=torch.float32, device="cuda")
+    ref = np.zeros_like(g.F)
+    S = np.zeros_like(g.F)
+    rng = np.random.default_rng(4)
+    for t in had:
+        gO = rng.standard_normal((9, t.ndata))
+        ref += oracle.had_grad(t, g.F, gO)
+        S += _grad_scale(t, g.F, gO)
+        tab = fk.Table.from_workload(t, precs=("bf16x3",))
+        run_bwd(tab, g.F, gO, "bf16x3", gF=gF, accumulate=True)
+    got = gF.double().cpu().numpy()
+    assert (np.abs(got - ref) / np.maximum(S, 1e-300)).max() <= BOUND["bf16x3"]

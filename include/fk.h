@@ -193,6 +193,17 @@ int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ld
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
                      void *gF, int accumulate, int prec, fk_stream stream);
 
+/*
+ * Sum of gradient buffers, for adjoints computed concurrently (on several
+ * streams, each into its own buffer) that must be combined in a fixed order:
+ *   out[e] (+)= parts[0][e] + parts[1][e] + ... + parts[nparts-1][e]
+ * parts: HOST array of nparts (1..64) DEVICE pointers to n elements each;
+ * out: DEVICE, n elements; element type double for FK_FP64, float otherwise.
+ * The sum runs in the listed order, so the result does not depend on timing.
+ */
+int fk_grad_sum(const void *const *parts, int nparts, long long n, void *out, int accumulate,
+                int prec, fk_stream stream);
+
 /* ---------------------------------------------------------------- chi^2 */
 
 /*

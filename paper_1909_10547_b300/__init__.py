@@ -168,6 +168,18 @@ def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False):
     return gF
 
 
+def grad_sum(parts, out, accumulate=False):
+    """out (+)= parts[0] + parts[1] + ... in that order (fk_grad_sum)."""
+    n = out.numel()
+    for p in parts:
+        if p.numel() != n or p.dtype != out.dtype or not p.is_contiguous():
+            raise ValueError("parts must be contiguous and match out")
+    arr = (ctypes.c_void_p * len(parts))(*[p.data_ptr() for p in parts])
+    prec = _lib.FK_FP64 if out.dtype == torch.float64 else _lib.FK_FP32
+    _lib.call("fk_grad_sum", arr, len(parts), n, _p(out), int(bool(accumulate)), prec, _stream())
+    return out
+
+
 class Cov:
     """Block-diagonal covariance factorised on the device (FP64)."""
 

@@ -24,6 +24,7 @@ SIGNATURES = {
     "fk_had_conv": [P, P, I, P, I, I, P],
     "fk_had_conv_noalloc": [P, P, I, P, I, I, P],
     "fk_conv_backward": [P, P, P, I, I, P, I, I, P],
+    "fk_grad_sum": [P, I, ctypes.c_longlong, P, I, I, P],
     "fk_cov_create": [P, P, I, PP],
     "fk_cov_destroy": [P],
     "fk_cov_size": [P],

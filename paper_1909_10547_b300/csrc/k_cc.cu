@@ -731,3 +731,48 @@ extern "C" int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void
         return had_noalloc_t<double>(t, (const double *)F, R, (double *)O, ldo, t->fk64, s);
     return had_noalloc_t<float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s);
 }
+
+// ----------------------------------------------------------------------------
+// Fixed-order sum of gradient buffers (fk_grad_sum).
+// ----------------------------------------------------------------------------
+namespace fk {
+namespace {
+constexpr int MAX_PARTS = 64;
+template <typename T>
+struct Parts {
+    const T *p[MAX_PARTS];
+};
+template <typename T>
+__global__ void k_grad_sum(Parts<T> parts, int nparts, long long n, T *__restrict__ out, int accumulate) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        T s = accumulate ? out[e] : T(0);
+        for (int k = 0; k < nparts; ++k) s += parts.p[k][e];
+        out[e] = s;
+    }
+}
+template <typename T>
+int grad_sum_t(const void *const *parts, int nparts, long long n, void *out, int accumulate, cudaStream_t s) {
+    Parts<T> P{};
+    for (int k = 0; k < nparts; ++k) P.p[k] = static_cast<const T *>(parts[k]);
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 148LL * 8));
+    k_grad_sum<T><<<blocks, 256, 0, s>>>(P, nparts, n, static_cast<T *>(out), accumulate);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+}  // namespace
+}  // namespace fk
+
+extern "C" int fk_grad_sum(const void *const *parts, int nparts, long long n, void *out, int accumulate,
+                           int prec, fk_stream stream) {
+    using namespace fk;
+    if (!parts || !out || nparts < 1 || nparts > MAX_PARTS || n < 0)
+        return fail(FK_EINVAL, "fk_grad_sum: bad arguments (1 <= nparts <= 64)");
+    for (int k = 0; k < nparts; ++k)
+        if (!parts[k]) return fail(FK_EINVAL, "fk_grad_sum: null part");
+    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_grad_sum: unknown precision");
+    if (n == 0) return FK_OK;
+    return prec == FK_FP64 ? grad_sum_t<double>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream)
+                           : grad_sum_t<float>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream);
+}

@@ -7,19 +7,25 @@ the convolution is the most time-consuming operation):
   loss      chi2[r] = (O_r - D)^T C^{-1} (O_r - D),  gO = d chi2 / d O  (FP64)
   backward  gF = sum_k conv_backward(table_k, F, gO[:, off_k : off_k + n_k])
 
-All three run in libfk.so kernels on the current CUDA stream.  capture()
-records each phase in a CUDA graph so a step costs three graph launches.
+All three run in libfk.so kernels.  The tables are spread over `nstreams`
+CUDA streams (balanced by their work) so that small tables run side by side
+on the 148 SMs: in the forward each table writes its own columns of O; in the
+backward each stream accumulates into its own gradient buffer and
+fk_grad_sum adds the buffers in a fixed order, so the result does not depend
+on how the streams interleave.  capture() records each phase in a CUDA graph
+(the streams become parallel branches), so a step costs three graph launches.
 """
 import numpy as np
 import torch
 
-from . import Cov, Table, chi2, conv, conv_backward, _lib
+from . import Cov, Table, _lib, chi2, conv, conv_backward, grad_sum
 
 NFL = 14
 
 
 class GlobalFit:
-    def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda"):
+    def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda",
+                 nstreams=8):
         """tables: workloads.DisTable/HadTable list sharing one x grid;
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
@@ -50,34 +56,73 @@ class GlobalFit:
         self.gF = torch.empty_like(self.F)
         self.chi2 = torch.empty(self.R, dtype=torch.float64, device=device)
         self.graphs = None
-        # algorithmic work per step (multiply-adds counted as 2 flops)
+        # algorithmic work per step (multiply-adds counted as 2 flops) and the
+        # table elements each phase streams
         fwd = bwd = 0
+        work = []
+        self.elems = {"had": 0, "dis": 0}
         for t in tables:
             if hasattr(t, "ca"):
                 e = t.ndata * t.nc * t.nx * t.nx
                 fwd += 2 * e * self.R
-                bwd += (2 * e + 4 * t.nc * t.nx * t.nx) * self.R
+                bwd += (4 * e) * self.R
+                self.elems["had"] += e
             else:
                 e = t.ndata * len(t.flav) * t.nx
                 fwd += 2 * e * self.R
                 bwd += 2 * e * self.R
+                self.elems["dis"] += e
+            work.append(e)
         self.flops = {"forward": fwd, "loss": 2 * int(sum(n * n for n in nd)) * self.R, "backward": bwd}
-        esz = 8 if prec == "fp64" else 4
-        self.table_bytes = {"forward": sum(t.ndata * (t.nc * t.nx * t.nx if hasattr(t, "ca") else len(t.flav) * t.nx)
-                                           for t in tables) * esz}
+        # streams: greedy assignment of tables (largest first) to the least
+        # loaded stream
+        self.nstreams = max(1, min(nstreams, len(tables)))
+        load = [0] * self.nstreams
+        self.groups = [[] for _ in range(self.nstreams)]
+        for k in sorted(range(len(tables)), key=lambda k: -work[k]):
+            s = int(np.argmin(load))
+            self.groups[s].append(k)
+            load[s] += work[k]
+        for grp in self.groups:
+            grp.sort()
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(self.nstreams)]
+        self.gF_parts = [torch.empty_like(self.F) for _ in range(self.nstreams)]
+
+    # -- helpers -------------------------------------------------------------
+    def _fan_out(self, body):
+        """Runs body(stream_index) on every side stream, forked from and
+        joined back to the current stream (graph-capture safe)."""
+        main = torch.cuda.current_stream()
+        start = torch.cuda.Event()
+        start.record(main)
+        ends = []
+        for s, st in enumerate(self.streams):
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                body(s)
+                e = torch.cuda.Event()
+                e.record(st)
+                ends.append(e)
+        for e in ends:
+            main.wait_event(e)
 
     # -- phases ------------------------------------------------------------
     def forward(self):
-        for k, t in enumerate(self.tabs):
-            conv(t, self.F, self.tprec[k], out=self.O[:, self.offs[k]:self.offs[k + 1]])
+        def body(s):
+            for k in self.groups[s]:
+                conv(self.tabs[k], self.F, self.tprec[k], out=self.O[:, self.offs[k]:self.offs[k + 1]])
+        self._fan_out(body)
 
     def loss(self):
         chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)
 
     def backward(self):
-        for k, t in enumerate(self.tabs):
-            conv_backward(t, self.F, self.gO[:, self.offs[k]:self.offs[k + 1]], self.tprec[k],
-                          gF=self.gF, accumulate=k > 0)
+        def body(s):
+            for n, k in enumerate(self.groups[s]):
+                conv_backward(self.tabs[k], self.F, self.gO[:, self.offs[k]:self.offs[k + 1]],
+                              self.tprec[k], gF=self.gF_parts[s], accumulate=n > 0)
+        self._fan_out(body)
+        grad_sum([self.gF_parts[s] for s in range(self.nstreams) if self.groups[s]], self.gF)
 
     def step(self):
         if self.graphs is not None:

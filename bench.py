@@ -39,6 +39,11 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="fit", choices=["fit", "stress"],
+                    help="fit: the fit step (default, the headline line); stress: one convolution "
+                         "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines")
+    ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
+    ap.add_argument("--replicas", type=int, default=1, help="stress case: replicas")
     return ap.parse_args()
 
 
@@ -250,9 +255,72 @@ def config_dict(g, prec):
             "graphs": True, "parallelism": "replicas only (one independent copy per rank)"}
 
 
+def run_stress(args):
+    """One convolution of the stress table, timed over graph replays: the
+    kernel-level roofline (HBM for the streaming path at small R, tensor pipe
+    for the tcgen05 path at large R)."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    t = W.stress_table(ndata=args.ndata)
+    tab = fk.Table.from_workload(t, precs=(args.prec,))
+    x = W.xgrid(50, 1e-7)
+    R = args.replicas
+    F = W.pdf_replicas(x, W.pdf_params(np.random.default_rng(1)), R, np.random.default_rng(2) if R > 1 else None)
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    Fd = torch.tensor(F, dtype=dt, device="cuda")
+    O = fk.conv(tab, Fd, args.prec)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fk.conv(tab, Fd, args.prec, out=O)
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    ms = e0.elapsed_time(e1) / args.steps
+    elems = t.fk.size
+    byts = elems * ESZ[args.prec]
+    flops = 2.0 * elems * R
+    pk, src = peaks()
+    tc = args.prec in ("bf16", "bf16x3", "tf32")
+    tpeak = (pk["bf16_tflops"] / (2.0 if args.prec == "tf32" else 1.0) if tc else
+             148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12 if args.prec == "fp32" else
+             148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12)
+    ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
+    if flops / byts < ridge:
+        ach = byts / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "algorithmic_bytes": byts}
+    else:
+        ach = flops / (ms * 1e-3) / 1e12
+        roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": ach / tpeak, "traffic": None}
+    roof["peak_source"] = src
+    line = {"metric": METRIC, "value": args.ndata * R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": f"hadronic stress table {args.ndata} x 196 channels x 50 x 50, one "
+                                   f"convolution, R={R}", "l2": "table larger than L2" if byts > 126e6 else
+                       "table fits in L2", "graphs": True},
+            "roofline": roof, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import torch
+    if args.case == "stress":
+        run_stress(args)
+        return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world, dist)

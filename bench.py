@@ -39,9 +39,12 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="fit", choices=["fit", "stress"],
+    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
-                         "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines")
+                         "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
+                         "serve: the served mixed workload (Poisson arrivals over 41 resident tables)")
+    ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
     ap.add_argument("--replicas", type=int, default=1, help="stress case: replicas")
     return ap.parse_args()
@@ -315,11 +318,136 @@ def run_stress(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served mixed workload: open-loop Poisson arrivals of convolution requests
+    on the 40 global-set tables plus the stress table, replica counts from
+    {1, 10, 100, 1000}, all tables resident, admission by a 150 GB budget.
+    Latency is measured by the client from submit to the poll that sees the
+    result; throughput is datapoint*replicas over first submit -> last
+    completion.  The same requests are then run one at a time through the
+    plain per-request path (H2D, fk_*_conv, D2H, synchronise) for comparison."""
+    import threading
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    g = workload()
+    prec = args.prec
+    tc = prec in ("bf16", "bf16x3", "tf32")
+    tables = list(g.tables) + [W.stress_table()]
+    tabs = []
+    for t in tables:
+        had = hasattr(t, "ca")
+        tabs.append(fk.Table.from_workload(t, precs=(prec,) if (had or not tc) else ("fp32",)))
+    tprec = [prec if (hasattr(t, "ca") or not tc) else "fp32" for t in tables]
+    nxg = [t.nxg for t in tables]
+    del tables
+    srv = fk.Server(budget_bytes=150 << 30, max_inflight=8)
+    ids = [srv.add_table(t) for t in tabs]
+    rng = np.random.default_rng(SEED + 1)
+    n = args.requests
+    which = rng.integers(0, len(tabs), n)
+    Rs = rng.choice(W.REPLICA_CHOICES, n)
+    arr = W.arrivals(rng, args.rate, n)
+    pool = {}  # a few PDF sets per (grid size, R), reused across requests
+    for k in range(n):
+        key = (nxg[which[k]], int(Rs[k]), tprec[which[k]])
+        if key not in pool:
+            x = g.x if key[0] == 50 else W.xgrid(key[0], 1e-7)
+            F = W.pdf_replicas(x, g.params, key[1], np.random.default_rng(key[1]))
+            pool[key] = F.astype(np.float64 if key[2] == "fp64" else np.float32)
+    work = [(int(which[k]), pool[(nxg[which[k]], int(Rs[k]), tprec[which[k]])], tprec[which[k]]) for k in range(n)]
+    units = sum(tabs[w].ndata * F.shape[0] for w, F, _ in work)
+
+    # warm-up: every table once
+    for k in range(len(tabs)):
+        srv.wait(srv.submit(ids[k], pool[next(key for key in pool if key[0] == nxg[k] and key[2] == tprec[k])], tprec[k]))
+
+    tickets = [None] * n
+    t_sub = np.zeros(n)
+    t_done = np.zeros(n)
+    done_flag = [False]
+
+    def poller():
+        outstanding = set()
+        nxt = 0
+        while nxt < n or outstanding:
+            while nxt < n and tickets[nxt] is not None:
+                outstanding.add(nxt)
+                nxt += 1
+            for k in list(outstanding):
+                ok, _ = srv.poll(tickets[k])
+                if ok:
+                    t_done[k] = time.perf_counter()
+                    outstanding.discard(k)
+            time.sleep(0.0001)
+        done_flag[0] = True
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for k, (w, F, p) in enumerate(work):
+        delay = t0 + arr[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        t_sub[k] = time.perf_counter()
+        tickets[k] = srv.submit(ids[w], F, p)
+    th.join()
+    lat = (t_done - t_sub) * 1e3
+    span = t_done.max() - t_sub.min()
+    st = srv.stats()
+    # saturation: the same requests in a closed loop that keeps WINDOW of them
+    # in flight (capacity of the server, independent of the arrival process)
+    WINDOW = 64
+    s0 = time.perf_counter()
+    inflight = []
+    for w, F, p in work:
+        if len(inflight) >= WINDOW:
+            srv.wait(inflight.pop(0), 600000)
+        inflight.append(srv.submit(ids[w], F, p))
+    for tk in inflight:
+        srv.wait(tk, 600000)
+    sat_span = time.perf_counter() - s0
+    srv.close()
+
+    # the plain per-request path, one request at a time, same requests
+    stream = torch.cuda.current_stream()
+    dev_cache = {}
+    t1 = time.perf_counter()
+    plain_lat = []
+    for w, F, p in work:
+        s0 = time.perf_counter()
+        dt = torch.float64 if p == "fp64" else torch.float32
+        Fd = torch.from_numpy(F).to("cuda", non_blocking=False)
+        O = fk.conv(tabs[w], Fd, p)
+        O.cpu()
+        plain_lat.append((time.perf_counter() - s0) * 1e3)
+    plain_span = time.perf_counter() - t1
+    line = {"metric": METRIC, "value": units / sat_span, "unit": UNIT, "n_gpus": 1, "steps": n,
+            "warmup": len(tabs), "ms_per_step": sat_span * 1e3 / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"served mix: {n} requests, Poisson {args.rate:g}/s, 40 global-set tables + "
+                                   "stress table 2000 x 196 x 50 x 50 resident, R in {1,10,100,1000}, "
+                                   "budget 150 GB", "max_inflight": 8,
+                       "value": "saturation throughput (closed loop, 64 requests in flight)"},
+            "serve": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "max_ms": float(lat.max()), "offered_rate": args.rate,
+                      "achieved_rate": n / span, "open_loop_value": units / span,
+                      "launches": st["launches"], "peak_bytes": st["peak_bytes"]},
+            "per_request_baseline": {"value": units / plain_span, "unit": UNIT,
+                                     "p50_ms": float(np.percentile(plain_lat, 50)),
+                                     "p99_ms": float(np.percentile(plain_lat, 99)),
+                                     "what": "one request at a time: H2D, fk conv, D2H, synchronise"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import torch
     if args.case == "stress":
         run_stress(args)
+        return
+    if args.case == "serve":
+        run_serve(args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

@@ -51,7 +51,10 @@ struct Request {
     bool done = false;
 };
 
-// Pinned host buffers recycled by size class (powers of two).
+// Pinned host buffers for request staging.  Pinning is slow (milliseconds per
+// call), so memory is pinned in slabs of at least 64 MiB and carved into
+// power-of-two size classes; freed buffers go back to their class's free list
+// and are reused.  Everything is unpinned when the server is destroyed.
 class PinnedPool {
    public:
     void *get(size_t n, size_t *cls) {
@@ -65,8 +68,17 @@ class PinnedPool {
             v.pop_back();
             return p;
         }
-        void *p = nullptr;
-        if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+        if (left_ < c) {
+            const size_t slab = std::max<size_t>(c, SLAB);
+            void *p = nullptr;
+            if (cudaHostAlloc(&p, slab, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+            slabs_.push_back(p);
+            cur_ = static_cast<char *>(p);
+            left_ = slab;
+        }
+        void *p = cur_;
+        cur_ += c;
+        left_ -= c;
         return p;
     }
     void put(void *p, size_t cls) {
@@ -75,13 +87,16 @@ class PinnedPool {
         free_[cls].push_back(p);
     }
     ~PinnedPool() {
-        for (auto &kv : free_)
-            for (void *p : kv.second) cudaFreeHost(p);
+        for (void *p : slabs_) cudaFreeHost(p);
     }
 
    private:
+    static constexpr size_t SLAB = 64u << 20;
     std::mutex mu_;
     std::map<size_t, std::vector<void *>> free_;
+    std::vector<void *> slabs_;
+    char *cur_ = nullptr;
+    size_t left_ = 0;
 };
 
 size_t pow2_class(size_t n) {

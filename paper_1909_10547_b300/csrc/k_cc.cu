@@ -316,25 +316,27 @@ constexpr size_t bwd_smem() {
 }
 
 // Accumulates the W tile for rows [e_b, e_b + rows) of the table, replicas
-// [r0, r0 + 64), into acc (thread (ty, tx) holds rows ty*8.., replicas tx*4..).
+// [r0, r0 + 64), data points [d_b, d_e), into acc (thread (ty, tx) holds rows
+// ty*8.., replicas tx*4..).
 template <typename T>
 __device__ __forceinline__ void bwd_w_tile(const TableView &tv, const T *__restrict__ fk,
                                            const T *__restrict__ gO, int ldgo, int R, long long e_b,
-                                           int rows, int r0, T *As, T *Gs, T (&acc)[8][4]) {
+                                           int rows, int r0, int d_b, int d_e, T *As, T *Gs,
+                                           T (&acc)[8][4]) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int dk = 0; dk < tv.ndata; dk += BKD) {
+    for (int dk = d_b; dk < d_e; dk += BKD) {
         for (int idx = threadIdx.x; idx < BKD * BET; idx += 256) {
             const int e = idx % BET, kd = idx / BET;
             const int d = dk + kd;
             T v = T(0);
-            if (d < tv.ndata && e < rows) v = fk[(size_t)d * tv.ldE + e_b + e];
+            if (d < d_e && e < rows) v = fk[(size_t)d * tv.ldE + e_b + e];
             As[kd * BET + e] = v;
         }
         for (int idx = threadIdx.x; idx < BKD * BRT; idx += 256) {
             const int kd = idx % BKD, rr = idx / BKD;
             const int d = dk + kd, r = r0 + rr;
             T v = T(0);
-            if (d < tv.ndata && r < R) v = gO[(size_t)r * ldgo + d];
+            if (d < d_e && r < R) v = gO[(size_t)r * ldgo + d];
             Gs[kd * BRT + rr] = v;
         }
         __syncthreads();
@@ -395,7 +397,8 @@ __global__ void __launch_bounds__(256) k_bwd_had(TableView tv, const T *__restri
     for (int p = 0; p < 8; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
-    bwd_w_tile<T>(tv, fk, gO, ldgo, R, (long long)c * nx2 + (long long)i0 * tv.nx, rows, r0, As, Gs, acc);
+    bwd_w_tile<T>(tv, fk, gO, ldgo, R, (long long)c * nx2 + (long long)i0 * tv.nx, rows, r0, 0, tv.ndata,
+                  As, Gs, acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int p = 0; p < 8; ++p)
@@ -441,39 +444,51 @@ __global__ void k_bwd_had_gather(TableView tv, const T *__restrict__ U, const T 
     gF[idx] = accumulate ? gF[idx] + s : s;
 }
 
-// DIS: grid (ceil(E/128), ceil(R/64)); gF[r][ca[k]][xmap[i]] += W[(k,i)][r].
-// gF must be zeroed beforehand when overwriting.
+// DIS: grid (ceil(E/128), ceil(R/64), nsplit): the data points are split in
+// nsplit ranges of dchunk; P[(split * R + r) * E + e] = sum over the range of
+// FK[d][e] gO[r][d].
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd_dis(TableView tv, const T *__restrict__ fk,
-                                                 const T *__restrict__ gO, int ldgo, int R,
-                                                 T *__restrict__ gF) {
+                                                 const T *__restrict__ gO, int ldgo, int R, int dchunk,
+                                                 T *__restrict__ P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *As = reinterpret_cast<T *>(smem_raw);
     T *Gs = As + BKD * BET;
     const long long e_b = (long long)blockIdx.x * BET;
     const int rows = (int)min((long long)BET, tv.E - e_b);
     const int r0 = blockIdx.y * BRT;
+    const int d_b = blockIdx.z * dchunk, d_e = min(tv.ndata, d_b + dchunk);
     T acc[8][4];
 #pragma unroll
     for (int p = 0; p < 8; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
-    bwd_w_tile<T>(tv, fk, gO, ldgo, R, e_b, rows, r0, As, Gs, acc);
+    bwd_w_tile<T>(tv, fk, gO, ldgo, R, e_b, rows, r0, d_b, d_e, As, Gs, acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const size_t fstride = (size_t)NFL * tv.nxg;
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int e = ty * 8 + p;
         if (e >= rows) continue;
-        const int eg = (int)(e_b + e);
-        const int k = eg / tv.nx, i = eg - k * tv.nx;
-        const int off = tv.ca[k] * tv.nxg + tv.xmap[i];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int r = r0 + tx * 4 + q;
-            if (r < R) gF[(size_t)r * fstride + off] += acc[p][q];
+            if (r < R) P[((size_t)blockIdx.z * R + r) * tv.E + e_b + e] = acc[p][q];
         }
     }
+}
+
+// gF[r][ca[k]][xmap[i]] (+)= sum_split P[split][r][(k,i)], splits in order.
+// gF must be zeroed beforehand when overwriting (grid points outside xmap).
+template <typename T>
+__global__ void k_bwd_dis_gather(TableView tv, const T *__restrict__ P, int nsplit, int R,
+                                 T *__restrict__ gF) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * tv.E) return;
+    const int r = (int)(idx / tv.E), e = (int)(idx - (long long)r * tv.E);
+    T s = T(0);
+    for (int z = 0; z < nsplit; ++z) s += P[((size_t)z * R + r) * tv.E + e];
+    const int k = e / tv.nx, i = e - k * tv.nx;
+    gF[((size_t)r * NFL + tv.ca[k]) * tv.nxg + tv.xmap[i]] += s;
 }
 
 // FP64 rows (staging, [rows][E]) -> padded stream layouts.
@@ -560,11 +575,24 @@ int bwd_cc_t(const fk_table *t, const T *F, const T *gO, int ldgo, int R, T *gF,
     const int rt = (R + BRT - 1) / BRT;
     constexpr size_t smem = bwd_smem<T>();
     if (t->kind == FK_KIND_DIS) {
+        // split the data points so that small tables still fill the GPU; the
+        // split depends on the table only
+        const int eb = (int)((t->E + BET - 1) / BET);
+        const int want = (2 * num_sms() + eb - 1) / eb;
+        const int dchunk = std::max(BKD, (t->ndata + want - 1) / want / BKD * BKD);
+        const int nsplit = (t->ndata + dchunk - 1) / dchunk;
+        Scratch scr(s);
+        T *P = nullptr;
+        FK_CUDA(scr.get(&P, (size_t)nsplit * R * t->E));
         if (!accumulate) FK_CUDA(cudaMemsetAsync(gF, 0, sizeof(T) * (size_t)R * NFL * t->nxg, s));
         int rc = set_smem<T>(k_bwd_dis<T>, smem);
         if (rc) return rc;
-        dim3 grid((unsigned)((t->E + BET - 1) / BET), rt);
-        k_bwd_dis<T><<<grid, 256, smem, s>>>(tv, fk, gO, ldgo, R, gF);
+        dim3 grid(eb, rt, nsplit);
+        k_bwd_dis<T><<<grid, 256, smem, s>>>(tv, fk, gO, ldgo, R, dchunk, P);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+        const long long n = (long long)R * t->E;
+        k_bwd_dis_gather<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tv, P, nsplit, R, gF);
         count_launch();
         FK_CUDA(cudaGetLastError());
         return FK_OK;

@@ -22,6 +22,8 @@ struct fk_cov {
     long long *d_loff = nullptr;
     int ntiles = 0;
     int *d_tile_blk = nullptr, *d_tile_i0 = nullptr;
+    int nzu = 0, ngu = 0;                          // work units of the two passes
+    int *d_zu = nullptr, *d_gu = nullptr, *d_zt = nullptr, *d_gt = nullptr;
     double *L = nullptr;     // per block n_k x n_k row-major, lower factor
     double *Linv = nullptr;  // same layout, L^{-1} (lower)
     size_t bytes = 0;
@@ -97,35 +99,42 @@ __global__ void __launch_bounds__(128) k_trinv(const long long *__restrict__ lof
     }
 }
 
+// A tile is 32 rows i0.. of one block.  Its contraction range is cut into
+// work units of at most UNIT_COLS columns so that no CTA carries a long chain
+// (the FP64 pipe is shared by the CTAs of an SM; one long tile would set the
+// kernel's length); the units' partial sums are added in unit order.
+constexpr int UNIT_COLS = 4 * CT;
+
 struct CovView {
     int n;
     const int *sizes, *offs, *tile_blk, *tile_i0;
     const long long *loff;
     const double *Linv;
+    const int *zu, *gu;     // units [u][3]: tile, m0, m1 (z pass, gradient pass)
+    const int *zt, *gt;     // per tile [t][2]: first unit, unit count
 };
 
-// grid (ntiles, ceil(R/32)), 256 threads: thread (ty, tx) -> rows i0+ty*4+p, replica r0+tx.
-// Z[(off+i)*R + r] = sum_{m<=i} X[i][m] (O[r][off+m] - D[off+m]);  zsq[tile*R + r] = sum_i Z^2.
+// grid (nunits, ceil(R/32)), 256 threads: thread (ty, tx) -> rows i0+ty*4+p, replica r0+tx.
+// Zp[(u*32 + row)*R + r] = sum_{m in [m0, m1)} X[i][m] (O[r][off+m] - D[off+m])
 template <typename TO>
-__global__ void __launch_bounds__(256) k_chi2_z(CovView cv, const TO *__restrict__ O,
-                                                const double *__restrict__ D, int R,
-                                                double *__restrict__ Z, double *__restrict__ zsq) {
-    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
+__global__ void __launch_bounds__(256) k_chi2_zpart(CovView cv, const TO *__restrict__ O,
+                                                    const double *__restrict__ D, int R,
+                                                    double *__restrict__ Zp) {
+    const int u = blockIdx.x, tile = cv.zu[3 * u], m0u = cv.zu[3 * u + 1], m1u = cv.zu[3 * u + 2];
+    const int k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
     const int nk = cv.sizes[k], off = cv.offs[k];
     const double *X = cv.Linv + cv.loff[k];
     const int r0 = blockIdx.y * CT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     __shared__ double Ls[CT][CT + 1], Rs[CT][CT + 1];
-    __shared__ double sq[8][CT];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int mend = min(i0 + CT, nk);
-    for (int m0 = 0; m0 < mend; m0 += CT) {
+    for (int m0 = m0u; m0 < m1u; m0 += CT) {
         for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
             const int a = idx / CT, b = idx % CT;
             const int i = i0 + a, m = m0 + b;
-            Ls[a][b] = (i < nk && m < nk) ? X[(size_t)i * nk + m] : 0.0;
+            Ls[a][b] = (i < nk && m < m1u) ? X[(size_t)i * nk + m] : 0.0;
             const int r = r0 + a;
-            Rs[b][a] = (r < R && m < nk) ? (double)O[(size_t)r * cv.n + off + m] - D[off + m] : 0.0;
+            Rs[b][a] = (r < R && m < m1u) ? (double)O[(size_t)r * cv.n + off + m] - D[off + m] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -137,20 +146,39 @@ __global__ void __launch_bounds__(256) k_chi2_z(CovView cv, const TO *__restrict
         __syncthreads();
     }
     const int r = r0 + tx;
-    double s = 0.0;
+    if (r < R) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int i = i0 + ty * 4 + p;
-        if (i < nk && r < R) {
-            Z[(size_t)(off + i) * R + r] = acc[p];
-            s = fma(acc[p], acc[p], s);
+        for (int p = 0; p < 4; ++p) Zp[((size_t)u * CT + ty * 4 + p) * R + r] = acc[p];
+    }
+}
+
+// grid (ntiles, ceil(R/32)): Z = sum of the tile's unit partials (in order),
+// zsq[tile*R + r] = sum over the tile's rows of Z^2.
+__global__ void __launch_bounds__(256) k_chi2_zred(CovView cv, const double *__restrict__ Zp, int R,
+                                                   double *__restrict__ Z, double *__restrict__ zsq) {
+    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
+    const int nk = cv.sizes[k], off = cv.offs[k];
+    const int u0 = cv.zt[2 * tile], nu = cv.zt[2 * tile + 1];
+    const int r = blockIdx.y * CT + (threadIdx.x & 31), ty = threadIdx.x >> 5;
+    __shared__ double sq[8][CT];
+    double s = 0.0;
+    if (r < R) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int row = ty * 4 + p, i = i0 + row;
+            double z = 0.0;
+            for (int u = 0; u < nu; ++u) z += Zp[((size_t)(u0 + u) * CT + row) * R + r];
+            if (i < nk) {
+                Z[(size_t)(off + i) * R + r] = z;
+                s = fma(z, z, s);
+            }
         }
     }
-    sq[ty][tx] = s;
+    sq[ty][threadIdx.x & 31] = s;
     __syncthreads();
     if (ty == 0 && r < R) {
         double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += sq[q][tx];
+        for (int q = 0; q < 8; ++q) t += sq[q][threadIdx.x];
         zsq[(size_t)tile * R + r] = t;
     }
 }
@@ -164,24 +192,24 @@ __global__ void k_chi2_sum(const double *__restrict__ zsq, int ntiles, int R, do
     chi2[r] = s;
 }
 
-// gO[r][off+i] = 2 sum_{m>=i} X[m][i] Z[off+m][r]
-template <typename TO>
-__global__ void __launch_bounds__(256) k_chi2_grad(CovView cv, const double *__restrict__ Z, int R,
-                                                   TO *__restrict__ gO) {
-    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
+// grid (nunits, ceil(R/32)): Gp[(u*32 + row)*R + r] = sum_{m in [m0, m1)} X[m][i] Z[off+m][r]
+__global__ void __launch_bounds__(256) k_chi2_gpart(CovView cv, const double *__restrict__ Z, int R,
+                                                    double *__restrict__ Gp) {
+    const int u = blockIdx.x, tile = cv.gu[3 * u], m0u = cv.gu[3 * u + 1], m1u = cv.gu[3 * u + 2];
+    const int k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
     const int nk = cv.sizes[k], off = cv.offs[k];
     const double *X = cv.Linv + cv.loff[k];
     const int r0 = blockIdx.y * CT;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     __shared__ double Ls[CT][CT + 1], Zs[CT][CT + 1];
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int m0 = i0; m0 < nk; m0 += CT) {
+    for (int m0 = m0u; m0 < m1u; m0 += CT) {
         for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
             const int a = idx / CT, b = idx % CT;
             const int m = m0 + a, i = i0 + b;
-            Ls[a][b] = (m < nk && i < nk) ? X[(size_t)m * nk + i] : 0.0;
+            Ls[a][b] = (m < m1u && i < nk) ? X[(size_t)m * nk + i] : 0.0;
             const int r = r0 + b;
-            Zs[a][b] = (m < nk && r < R) ? Z[(size_t)(off + m) * R + r] : 0.0;
+            Zs[a][b] = (m < m1u && r < R) ? Z[(size_t)(off + m) * R + r] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -192,11 +220,33 @@ __global__ void __launch_bounds__(256) k_chi2_grad(CovView cv, const double *__r
         }
         __syncthreads();
     }
-    // stage for coalesced stores along i
+    const int r = r0 + tx;
+    if (r < R) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) Gp[((size_t)u * CT + ty * 4 + p) * R + r] = acc[p];
+    }
+}
+
+// grid (ntiles, ceil(R/32)): gO[r][off+i] = 2 * sum of the tile's unit partials (in order)
+template <typename TO>
+__global__ void __launch_bounds__(256) k_chi2_gred(CovView cv, const double *__restrict__ Gp, int R,
+                                                   TO *__restrict__ gO) {
+    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
+    const int nk = cv.sizes[k], off = cv.offs[k];
+    const int u0 = cv.gt[2 * tile], nu = cv.gt[2 * tile + 1];
+    const int r0 = blockIdx.y * CT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     __shared__ double out[CT][CT + 1];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) out[tx][ty * 4 + p] = 2.0 * acc[p];
+    for (int p = 0; p < 4; ++p) {
+        const int row = ty * 4 + p;
+        double g = 0.0;
+        if (r0 + tx < R)
+            for (int u = 0; u < nu; ++u) g += Gp[((size_t)(u0 + u) * CT + row) * R + r0 + tx];
+        out[tx][row] = 2.0 * g;
+    }
     __syncthreads();
+    // stage for coalesced stores along i
     for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
         const int rr = idx / CT, ii = idx % CT;
         const int r = r0 + rr, i = i0 + ii;
@@ -205,7 +255,8 @@ __global__ void __launch_bounds__(256) k_chi2_grad(CovView cv, const double *__r
 }
 
 CovView cview(const fk_cov *c) {
-    return CovView{c->n, c->d_sizes, c->d_offs, c->d_tile_blk, c->d_tile_i0, c->d_loff, c->Linv};
+    return CovView{c->n, c->d_sizes, c->d_offs, c->d_tile_blk, c->d_tile_i0, c->d_loff, c->Linv,
+                   c->d_zu, c->d_gu, c->d_zt, c->d_gt};
 }
 
 void cov_free(fk_cov *c) {
@@ -215,9 +266,31 @@ void cov_free(fk_cov *c) {
     cudaFree(c->d_loff);
     cudaFree(c->d_tile_blk);
     cudaFree(c->d_tile_i0);
+    cudaFree(c->d_zu);
+    cudaFree(c->d_gu);
+    cudaFree(c->d_zt);
+    cudaFree(c->d_gt);
     cudaFree(c->L);
     cudaFree(c->Linv);
     delete c;
+}
+
+// Work units of the two passes: z needs columns [0, min(i0+32, n)) of the
+// tile's rows, the gradient columns [i0, n); each range cut every UNIT_COLS.
+void make_units(const std::vector<int> &tb, const std::vector<int> &ti, const std::vector<int> &sizes,
+                bool grad, std::vector<int> &units, std::vector<int> &per_tile) {
+    for (size_t t = 0; t < tb.size(); ++t) {
+        const int n = sizes[tb[t]], i0 = ti[t];
+        const int b = grad ? i0 : 0, e = grad ? n : std::min(i0 + CT, n);
+        per_tile.push_back((int)(units.size() / 3));
+        int cnt = 0;
+        for (int m = b; m < e; m += UNIT_COLS, ++cnt) {
+            units.push_back((int)t);
+            units.push_back(m);
+            units.push_back(std::min(m + UNIT_COLS, e));
+        }
+        per_tile.push_back(cnt);
+    }
 }
 
 int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
@@ -270,6 +343,20 @@ int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
     e = e ? e : cudaMemcpy(c->d_tile_blk, tb.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->d_tile_i0, ti.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->L, C, sizeof(double) * el, cudaMemcpyHostToDevice);
+    std::vector<int> zu, zt, gu, gt;
+    make_units(tb, ti, c->sizes, false, zu, zt);
+    make_units(tb, ti, c->sizes, true, gu, gt);
+    c->nzu = (int)zu.size() / 3;
+    c->ngu = (int)gu.size() / 3;
+    if (!e && (cudaMalloc(&c->d_zu, sizeof(int) * zu.size()) || cudaMalloc(&c->d_gu, sizeof(int) * gu.size()) ||
+               cudaMalloc(&c->d_zt, sizeof(int) * zt.size()) || cudaMalloc(&c->d_gt, sizeof(int) * gt.size()))) {
+        cudaFree(d_info);
+        return cleanup(fail(FK_ENOMEM, "fk_cov_create: work units"));
+    }
+    e = e ? e : cudaMemcpy(c->d_zu, zu.data(), sizeof(int) * zu.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_gu, gu.data(), sizeof(int) * gu.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_zt, zt.data(), sizeof(int) * zt.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_gt, gt.data(), sizeof(int) * gt.size(), cudaMemcpyHostToDevice);
     if (e) {
         cudaFree(d_info);
         return cleanup(cuda_fail(e, "fk_cov_create: copy"));
@@ -300,19 +387,26 @@ template <typename TO>
 int chi2_t(const fk_cov *c, const TO *O, const double *D, int R, double *out, TO *gO,
            cudaStream_t s) {
     Scratch scr(s);
-    double *Z = nullptr, *zsq = nullptr;
+    double *Z = nullptr, *zsq = nullptr, *part = nullptr;
     FK_CUDA(scr.get(&Z, (size_t)c->n * R));
     FK_CUDA(scr.get(&zsq, (size_t)c->ntiles * R));
+    FK_CUDA(scr.get(&part, (size_t)std::max(c->nzu, c->ngu) * CT * R));
     CovView cv = cview(c);
-    dim3 grid(c->ntiles, (R + CT - 1) / CT);
-    k_chi2_z<TO><<<grid, 256, 0, s>>>(cv, O, D, R, Z, zsq);
+    const int rt = (R + CT - 1) / CT;
+    k_chi2_zpart<TO><<<dim3(c->nzu, rt), 256, 0, s>>>(cv, O, D, R, part);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    k_chi2_zred<<<dim3(c->ntiles, rt), 256, 0, s>>>(cv, part, R, Z, zsq);
     count_launch();
     FK_CUDA(cudaGetLastError());
     k_chi2_sum<<<(R + 127) / 128, 128, 0, s>>>(zsq, c->ntiles, R, out);
     count_launch();
     FK_CUDA(cudaGetLastError());
     if (gO) {
-        k_chi2_grad<TO><<<grid, 256, 0, s>>>(cv, Z, R, gO);
+        k_chi2_gpart<<<dim3(c->ngu, rt), 256, 0, s>>>(cv, Z, R, part);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+        k_chi2_gred<TO><<<dim3(c->ntiles, rt), 256, 0, s>>>(cv, part, R, gO);
         count_launch();
         FK_CUDA(cudaGetLastError());
     }

@@ -78,6 +78,9 @@ struct TcPack {
     CUtensorMap map_hi;   // (the type is 128-byte aligned)
     CUtensorMap map_lo;
     CUtensorMap map_f32;
+    // the same tensors with boxes of n_rows / 2 rows: each CTA of a pair
+    // running 2-SM MMAs loads one half of every B tile
+    CUtensorMap half_hi, half_lo, half_f32;
 };
 
 struct TcLayout {

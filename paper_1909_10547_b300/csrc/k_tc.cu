@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <set>
 
@@ -42,6 +43,7 @@ constexpr int TC_M = 128;   // replicas per tile (MMA M)
 constexpr int TC_THREADS = 192;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr int KPAD = 16;    // K padding of each group (a multiple of both K steps)
+constexpr int PW_SLACK = 2; // stages of slack for a producer-side accumulator wait
 
 // ---------------------------------------------------------------- PTX ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -73,16 +75,31 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Waits for the phase of the given parity, polling only the barrier (the
-// hardware suspends the thread between polls).  Gives up after WAIT_NS and
-// raises the device error word; `dead` latches per thread, so after one
-// time-out a role stops waiting at once and the CTA drains within a few
-// time-outs instead of waiting on every remaining barrier.
+// As mbar_try, but the thread may stay suspended in the barrier unit for up
+// to `ns` nanoseconds until the phase completes: a waiting thread issues no
+// instructions, so it takes no issue slots from the producer and MMA threads
+// that share its scheduler.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t SLEEP_NS = 100000;  // suspend-time hint per poll
+// Waits for the phase of the given parity.  Gives up after WAIT_NS and raises
+// the device error word; `dead` latches per thread, so after one time-out a
+// role stops waiting at once and the CTA drains within a few time-outs
+// instead of waiting on every remaining barrier.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, bool &dead) {
     if (mbar_try(bar, parity)) return true;
     if (dead) return false;
     const uint64_t t0 = gtimer();
-    while (!mbar_try(bar, parity)) {
+    while (!mbar_try_sleep(bar, parity, SLEEP_NS)) {
         if (gtimer() - t0 > WAIT_NS) {
             dead = true;
             atomicExch(&g_fk_device_error, 1);
@@ -98,6 +115,47 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
         "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
         : "memory");
+}
+// As tma_load_2d for a CTA pair running 2-SM MMAs: the copy lands in this
+// CTA's shared memory and completes its bytes on the mbarrier at `bar`, a
+// shared::cluster address that may be in the peer CTA.
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                                 int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+// shared::cluster address of this CTA's shared-memory address `addr` in CTA `rank`
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// arrive on an mbarrier given by its shared::cluster address (any CTA of the cluster)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of both CTAs of the cluster; orders mbarrier initialisation
+// and shared-memory use across the pair.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 __device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
@@ -118,27 +176,78 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     d |= (uint64_t)2 << 61;             // SWIZZLE_128B
     return d;
 }
-template <int PREC>
+// D[tmem] (+)= A * B^T for one K step.  CG = 1: M = 128 rows of this CTA.
+// CG = 2 (issued by the even CTA of a pair): M = 256, rows 0..127 from the even
+// CTA's A and rows 128..255 from the odd CTA's A at the same shared-memory
+// offset; the B rows (the N axis) are split in halves the same way; each CTA's
+// TMEM receives the D rows of its own A rows over all N columns.
+template <int PREC, int CG>
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t accum) {
     if (PREC == FK_TF32) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
+        if (CG == 2)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accum)
+                : "memory");
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accum)
+                : "memory");
     } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(accum)
-            : "memory");
+        if (CG == 2)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accum)
+                : "memory");
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                "l"(a), "l"(b), "r"(idesc), "r"(accum)
+                : "memory");
     }
 }
+// Arrives on the mbarrier (of this CTA) once every MMA issued so far by this
+// thread has completed.
+template <int CG>
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
+    if (CG == 2)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+}
+// As mma_commit<2>, arriving on the mbarrier at this offset in both CTAs of the pair.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"((uint16_t)0x3)
         : "memory");
+}
+template <int CG>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot) {
+    if (CG == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(slot) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(slot) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+template <int CG>
+__device__ __forceinline__ void tmem_free(uint32_t tmem) {
+    if (CG == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
@@ -162,9 +271,14 @@ struct Tr {
     static constexpr int KC = 128 / ESZ;      // K elements per 128-byte swizzled row
     static constexpr int KSTEP = 32 / ESZ;    // K per MMA instruction
     static constexpr int NOPS = X3 ? 2 : 1;   // operand copies (hi, lo)
-    static constexpr int STAGES = X3 ? 2 : 4;
     static constexpr uint32_t FMT = PREC == FK_TF32 ? 2u : 1u;  // TF32 : BF16
 };
+// Pipeline depth: a CTA of a pair holds half of each B tile, so its stages
+// are smaller and more of them fit.
+template <int PREC, int CL>
+__host__ __device__ constexpr int tc_stages() {
+    return CL == 2 ? (Tr<PREC>::X3 ? 3 : 6) : (Tr<PREC>::X3 ? 2 : 4);
+}
 
 struct TcParams {
     int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
@@ -181,23 +295,49 @@ struct TcParams {
 // (with the transposed packing, i stands for x_j and g for the second flavour)
 enum { MODE_FWD = 0, MODE_ADJ = 1 };
 
-template <int PREC>
+template <int PREC, int CL>
 size_t tc_smem_bytes(int n_rows) {
-    const size_t stage = (size_t)Tr<PREC>::NOPS * (TC_M * 128 + (size_t)n_rows * 128);
-    return 1024 + Tr<PREC>::STAGES * stage + 256;
+    const size_t stage = (size_t)Tr<PREC>::NOPS * (TC_M * 128 + (size_t)(n_rows / CL) * 128);
+    return 1024 + tc_stages<PREC, CL>() * stage + 256;
 }
 
-template <int PREC, int G, int MODE>
+// One work item is a (replica tile, data tile) pair of the product
+// Y_g = A_g B_g^T (A: packed PDFs, B: packed table), reduced by the epilogue.
+//  CL = 1: one CTA per tile, 128 x n_rows MMAs.
+//  CL = 2: a cluster of two CTAs owns replica tiles 2u and 2u+1 of one data
+//  tile and runs 256 x n_rows MMAs on both SMs' tensor cores: each CTA loads
+//  its own 128 A rows and one half of the B rows, so every SM takes in half of
+//  the table tile.  The even CTA issues the MMAs; the copies of both CTAs
+//  complete on its `full` barriers, its commits release `empty` and signal
+//  `accf` in both CTAs, and both CTAs' epilogues release its `acce`.
+template <int PREC, int G, int MODE, int CL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
          const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
          TcParams p) {
     using T = Tr<PREC>;
-    constexpr int S = T::STAGES;
+    constexpr int S = tc_stages<PREC, CL>();
+    const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    // work items: tiles (CL = 1) or pairs of replica tiles (CL = 2)
+    const int w_first = CL == 2 ? (int)cluster_id() : (int)blockIdx.x;
+    const int w_step = CL == 2 ? (int)cluster_count() : (int)gridDim.x;
+    const int w_count = p.ntiles / CL;
+    auto tile_of = [&](int w, int &rt, int &nt) {
+        if (CL == 2) {
+            const int half = p.nrt / 2;
+            nt = w / half;
+            rt = 2 * (w % half) + (int)rank;
+        } else {
+            rt = w % p.nrt;
+            nt = w / p.nrt;
+        }
+    };
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)p.n_rows * 128;
+    const int b_rows = p.n_rows / CL;  // B rows held by this CTA
+    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)b_rows * 128;
     const uint32_t stage_bytes = T::NOPS * (a_bytes + b_bytes);
     const uint32_t bar0 = base + S * stage_bytes;
     auto full = [&](int s) { return bar0 + 8u * s; };
@@ -217,7 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf(b), 1);
-            mbar_init(acce(b), 4);
+            mbar_init(acce(b), 4 * CL);  // the epilogue warps of every CTA of the pair
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -228,58 +368,132 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             prefetch_map(&mapB2);
         }
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                         smem_u32((const void *)tmem_slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 1) tmem_alloc<CL>(smem_u32((const void *)tmem_slot));
     tc_fence_before();
-    __syncthreads();
+    if (CL == 2)
+        cluster_sync();  // the peer's barriers exist before any copy or arrive targets them
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // Accumulator hand-off.  Use u of the double-buffered accumulator may
+    // start once the epilogue has released use u - 2 (the same buffer).  For
+    // group g that wait is made by the (even CTA's) producer before it loads
+    // the stage holding the group's first K step: the MMAs reach that stage
+    // only through its full barrier, so they are ordered after the release,
+    // and the MMA thread itself does not wait on the epilogue.  The producer
+    // runs S stages ahead of the MMAs, so it takes the wait only where use
+    // u - 2 ends at least S + PW_SLACK stages before that stage (in this tile
+    // or an earlier one): then the release is due and the wait costs nothing,
+    // and use u - 2 needs no stage the producer has yet to load.  For groups
+    // that follow closer behind (short groups), the MMA thread waits at the
+    // group's first K step, with the stage already loaded.
+    uint32_t pwait = 0;
+    for (int g = 0; g < p.ngroups; ++g) {
+        int u2 = g - 2, back = 0;  // group of use u - 2, tiles back
+        while (u2 < 0) {
+            u2 += p.ngroups;
+            ++back;
+        }
+        const int e2 = (p.kend[u2] + T::KC - 1) / T::KC - back * p.nchunks;  // stage after its last
+        if (p.kbeg[g] / T::KC - S - e2 >= PW_SLACK) pwait |= 1u << g;
+    }
+
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
-        int it = 0;
+        int it = 0, pgc = 0;  // pgc: accumulator uses (groups) reached so far
         bool ok = true;
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            const int rt = tile % p.nrt, nt = tile / p.nrt;
+        for (int w = w_first; w < w_count && ok; w += w_step) {
+            int rt, nt;
+            tile_of(w, rt, nt);
+            const int brow = nt * p.n_rows + (int)rank * b_rows;
+            int pg = 0;  // next group whose first stage is still to be loaded
             for (int q = 0; q < p.nchunks; ++q, ++it) {
                 const int s = it % S;
+                if (leader) {
+                    // the accumulator of every group starting in this stage
+                    // must be free before the MMAs can read the stage
+                    while (pg < p.ngroups && p.kbeg[pg] < (q + 1) * T::KC) {
+                        if (((pwait >> pg) & 1u) && !mbar_wait(acce(pgc & 1), ((pgc >> 1) & 1) ^ 1, dead)) {
+                            ok = false;
+                            break;
+                        }
+                        ++pg;
+                        ++pgc;
+                    }
+                    if (!ok) break;
+                }
                 if (!mbar_wait(empty(s), ((it / S) & 1) ^ 1, dead)) {
                     ok = false;
                     break;
                 }
                 const uint32_t st = base + s * stage_bytes;
-                mbar_expect_tx(full(s), stage_bytes);
-                tma_load_2d(st, &mapA, full(s), q * T::KC, rt * TC_M);
-                tma_load_2d(st + a_bytes, &mapB, full(s), q * T::KC, nt * p.n_rows);
-                if (T::X3) {
-                    tma_load_2d(st + a_bytes + b_bytes, &mapA2, full(s), q * T::KC, rt * TC_M);
-                    tma_load_2d(st + 2 * a_bytes + b_bytes, &mapB2, full(s), q * T::KC, nt * p.n_rows);
+                if (CL == 2) {
+                    const uint32_t fb = mapa(full(s), 0);
+                    if (leader) mbar_expect_tx(full(s), 2 * stage_bytes);
+                    tma_load_2d_pair(st, &mapA, fb, q * T::KC, rt * TC_M);
+                    tma_load_2d_pair(st + a_bytes, &mapB, fb, q * T::KC, brow);
+                    if (T::X3) {
+                        tma_load_2d_pair(st + a_bytes + b_bytes, &mapA2, fb, q * T::KC, rt * TC_M);
+                        tma_load_2d_pair(st + 2 * a_bytes + b_bytes, &mapB2, fb, q * T::KC, brow);
+                    }
+                } else {
+                    mbar_expect_tx(full(s), stage_bytes);
+                    tma_load_2d(st, &mapA, full(s), q * T::KC, rt * TC_M);
+                    tma_load_2d(st + a_bytes, &mapB, full(s), q * T::KC, brow);
+                    if (T::X3) {
+                        tma_load_2d(st + a_bytes + b_bytes, &mapA2, full(s), q * T::KC, rt * TC_M);
+                        tma_load_2d(st + 2 * a_bytes + b_bytes, &mapB2, full(s), q * T::KC, brow);
+                    }
                 }
             }
+        }
+        if (ok && CL == 2) {
+            // the last stages are released by commits of the peer's MMA
+            // issuer: take them before the CTA may exit
+            for (int j = it > S ? it - S : 0; j < it; ++j)
+                if (!mbar_wait(empty(j % S), (j / S) & 1, dead)) break;
         }
         if (!ok) {
-            // let the copies already issued land before the CTA exits
-            for (int k = 1; k <= S && it - k >= 0; ++k) {
-                const int j = it - k;
+            if (leader) {
+                // let the copies already issued land before the CTA exits
+                // (for a pair this includes the odd CTA's halves)
+                for (int k = 1; k <= S && it - k >= 0; ++k) {
+                    const int j = it - k;
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try(full(j % S), (j / S) & 1) && gtimer() - t0 < WAIT_NS) {
+                    }
+                }
+            } else {
+                // the odd CTA's copies complete on the even CTA's barriers:
+                // give them a bounded time to land
                 const uint64_t t0 = gtimer();
-                while (!mbar_try(full(j % S), (j / S) & 1) && gtimer() - t0 < WAIT_NS) {
+                while (gtimer() - t0 < 1000000ull) {
                 }
             }
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
         // ------------------------------------------------ MMA issuer
+        // The tensor pipe is fed best by straight-line MMA issue: a stage in
+        // which no group needs the MMA thread to wait for the epilogue runs a
+        // branch-light path; only stages where such a (short) group starts
+        // take the path with the wait.
         const uint32_t idesc = (1u << 4) | (T::FMT << 7) | (T::FMT << 10) |
-                               ((uint32_t)(p.n_rows >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+                               ((uint32_t)(p.n_rows >> 3) << 17) | ((uint32_t)((CL * TC_M) >> 4) << 24);
+        const uint32_t mwait = ~pwait & ((1u << p.ngroups) - 1u);  // groups the MMA thread waits for
+        // K index where the first MMA-waited group at or after group h starts
+        auto next_wait_k = [&](int h) -> int {
+            const uint32_t m = h < 32 ? mwait >> h : 0u;
+            return m ? p.kbeg[h + __ffs(m) - 1] : 0x7fffffff;
+        };
         int it = 0, gc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
+        for (int w = w_first; w < w_count && ok; w += w_step) {
             // the current group's K range lives in registers; the parameter
             // arrays are read only when a group ends
             int g = 0, kb = p.kbeg[0], ke = p.kend[0];
+            int kw = next_wait_k(0);
             for (int q = 0; q < p.nchunks && ok; ++q, ++it) {
                 const int s = it % S;
                 if (!mbar_wait(full(s), (it / S) & 1, dead)) {
@@ -288,46 +502,86 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t st = base + s * stage_bytes;
+                if (kw >= (q + 1) * T::KC) {
 #pragma unroll
-                for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
-                    const int k = q * T::KC + ks * T::KSTEP;
-                    if (g >= p.ngroups) break;  // K padding after the last group
-                    const int b = gc & 1;
-                    if (k == kb) {
-                        if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, dead)) {
-                            ok = false;
-                            break;
+                    for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
+                        const int k = q * T::KC + ks * T::KSTEP;
+                        if (g >= p.ngroups) break;  // K padding after the last group
+                        const int b = gc & 1;
+                        const uint32_t d = tmem + (uint32_t)(b * 256);
+                        const uint32_t off = (uint32_t)ks * 32u;
+                        const uint64_t ah = sw128_desc(st + off);
+                        const uint64_t bh = sw128_desc(st + a_bytes + off);
+                        mma<PREC, CL>(d, ah, bh, idesc, k != kb);
+                        if (T::X3) {
+                            const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
+                            const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
+                            mma<PREC, CL>(d, ah, bl, idesc, 1);
+                            mma<PREC, CL>(d, al, bh, idesc, 1);
                         }
-                        tc_fence_after();
-                    }
-                    const uint32_t d = tmem + (uint32_t)(b * 256);
-                    const uint32_t off = (uint32_t)ks * 32u;
-                    const uint64_t ah = sw128_desc(st + off);
-                    const uint64_t bh = sw128_desc(st + a_bytes + off);
-                    mma<PREC>(d, ah, bh, idesc, k != kb);
-                    if (T::X3) {
-                        const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
-                        const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
-                        mma<PREC>(d, ah, bl, idesc, 1);
-                        mma<PREC>(d, al, bh, idesc, 1);
-                    }
-                    if (k + T::KSTEP == ke) {
-                        mma_commit(accf(b));
-                        ++gc;
-                        ++g;
-                        if (g < p.ngroups) {
-                            kb = p.kbeg[g];
-                            ke = p.kend[g];
+                        if (k + T::KSTEP == ke) {
+                            if (CL == 2)
+                                mma_commit_pair(accf(b));
+                            else
+                                mma_commit<1>(accf(b));
+                            ++gc;
+                            ++g;
+                            if (g < p.ngroups) {
+                                kb = p.kbeg[g];
+                                ke = p.kend[g];
+                            }
                         }
                     }
+                } else {
+                    for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
+                        const int k = q * T::KC + ks * T::KSTEP;
+                        if (g >= p.ngroups) break;
+                        const int b = gc & 1;
+                        if (k == kb && ((mwait >> g) & 1u)) {
+                            if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, dead)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                        }
+                        const uint32_t d = tmem + (uint32_t)(b * 256);
+                        const uint32_t off = (uint32_t)ks * 32u;
+                        const uint64_t ah = sw128_desc(st + off);
+                        const uint64_t bh = sw128_desc(st + a_bytes + off);
+                        mma<PREC, CL>(d, ah, bh, idesc, k != kb);
+                        if (T::X3) {
+                            const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
+                            const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
+                            mma<PREC, CL>(d, ah, bl, idesc, 1);
+                            mma<PREC, CL>(d, al, bh, idesc, 1);
+                        }
+                        if (k + T::KSTEP == ke) {
+                            if (CL == 2)
+                                mma_commit_pair(accf(b));
+                            else
+                                mma_commit<1>(accf(b));
+                            ++gc;
+                            ++g;
+                            if (g < p.ngroups) {
+                                kb = p.kbeg[g];
+                                ke = p.kend[g];
+                            }
+                        }
+                    }
+                    // the next wait is at a group that has not started yet:
+                    // group g itself if it begins at the next stage
+                    kw = next_wait_k(g < p.ngroups && kb >= (q + 1) * T::KC ? g : g + 1);
                 }
-                mma_commit(empty(s));
+                if (CL == 2)
+                    mma_commit_pair(empty(s));
+                else
+                    mma_commit<1>(empty(s));
             }
         }
         // TMEM is freed only after every MMA issued here has completed
-        mma_commit(drain);
+        mma_commit<CL>(drain);
         const uint64_t t0 = gtimer();
-        while (!mbar_try(drain, 0)) {
+        while (!mbar_try_sleep(drain, 0, SLEEP_NS)) {
             if (gtimer() - t0 > WAIT_NS) {
                 atomicExch(&g_fk_device_error, 1);
                 break;
@@ -337,10 +591,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;
         const int rl = quarter * 32 + lane;
+        const uint32_t acce0 = CL == 2 ? mapa(acce(0), 0) : acce(0);
         int gc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < p.ntiles && ok; tile += gridDim.x) {
-            const int rt = tile % p.nrt, nt = tile / p.nrt;
+        for (int w = w_first; w < w_count && ok; w += w_step) {
+            int rt, nt;
+            tile_of(w, rt, nt);
             const int r = rt * TC_M + rl;
             float acc[G];
 #pragma unroll
@@ -401,7 +657,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acce(b));
+                if (lane == 0) {
+                    if (CL == 2)
+                        mbar_arrive_cluster(acce0 + 8u * b);
+                    else
+                        mbar_arrive(acce(b));
+                }
             }
             if (!ok) break;
             if (MODE == MODE_FWD && r < p.R) {
@@ -414,10 +675,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     }
     tc_fence_before();
-    __syncthreads();
+    if (CL == 2)
+        cluster_sync();  // no MMA, commit, copy or arrive of the pair still targets this CTA
+    else
+        __syncthreads();
     tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    if (warp == 1) tmem_free<CL>(tmem);
 }
 
 // ------------------------------------------------------------ packing ----
@@ -566,6 +829,22 @@ int make_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long
     return FK_OK;
 }
 
+// Dynamic shared memory of a tensor-core launch: at least half of an SM's,
+// so that one CTA runs per SM.  Each CTA allocates all 512 TMEM columns; a
+// second CTA on the same SM would wait in its allocation for the first to
+// finish, and with CTA pairs such waits could form a cycle.
+size_t one_per_sm(size_t need) {
+    static size_t floor_bytes = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        floor_bytes = per_sm > 0 ? (size_t)per_sm / 2 + 1024 : 0;
+    });
+    return std::max(need, floor_bytes);
+}
+
 int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -584,27 +863,95 @@ int opt_in_smem(K kernel, size_t bytes) {
     return FK_OK;
 }
 
+// Largest number of co-resident 2-CTA clusters of this kernel (cached per
+// kernel and shared-memory size); 0 if the query fails.
+template <typename K>
+int max_clusters(K kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> known;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair((const void *)kernel, smem);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * 74, 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    known[key] = n;
+    return n;
+}
+
+// The B operand maps of one packing for precision PREC: full tiles (first,
+// second operand copy) and half tiles for the CTA-pair launch.
+struct BMaps {
+    const CUtensorMap *b, *b2, *h, *h2;
+};
+template <int PREC>
+BMaps b_maps(const TcPack &pk) {
+    if (PREC == FK_TF32) return {&pk.map_f32, &pk.map_f32, &pk.half_f32, &pk.half_f32};
+    if (PREC == FK_BF16X3) return {&pk.map_hi, &pk.map_lo, &pk.half_hi, &pk.half_lo};
+    return {&pk.map_hi, &pk.map_hi, &pk.half_hi, &pk.half_hi};
+}
+
 template <int PREC, int G, int MODE>
-int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
-              const CUtensorMap &mB2, const TcParams &p, cudaStream_t s) {
-    const size_t smem = tc_smem_bytes<PREC>(t->tc.n_rows);
-    // opt in once at the largest tile (n_rows = 256) so that every table fits
-    int rc = opt_in_smem(k_tc<PREC, G, MODE>, tc_smem_bytes<PREC>(256));
+int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const BMaps &mb,
+              const TcParams &p, cudaStream_t s) {
+    // CTA pairs (256-row MMAs on two SMs) whenever the replica tiles pair up
+    if (p.nrt % 2 == 0) {
+        auto kern = k_tc<PREC, G, MODE, 2>;
+        const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(t->tc.n_rows));
+        // opt in once at the largest tile (n_rows = 256) so that every table fits
+        int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 2>(256));
+        if (rc) return rc;
+        const int nc = std::min(p.ntiles / 2, max_clusters(kern, smem));
+        if (nc > 0) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(2 * nc, 1, 1);
+            cfg.blockDim = dim3(TC_THREADS, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            FK_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mA2, *mb.h, *mb.h2, p));
+            count_launch();
+            return FK_OK;
+        }
+    }
+    auto kern = k_tc<PREC, G, MODE, 1>;
+    int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;
     const int grid = std::min(p.ntiles, sm_count());
-    k_tc<PREC, G, MODE><<<grid, TC_THREADS, smem, s>>>(mA, mA2, mB, mB2, p);
+    kern<<<grid, TC_THREADS, one_per_sm(tc_smem_bytes<PREC, 1>(t->tc.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
 }
 
 template <int PREC, int MODE>
-int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
-                const CUtensorMap &mB2, const TcParams &p, cudaStream_t s) {
+int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const TcPack &pk,
+                const TcParams &p, cudaStream_t s) {
+    const BMaps mb = b_maps<PREC>(pk);
     switch (t->tc.G) {
-        case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mB, mB2, p, s);
-        case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mB, mB2, p, s);
-        case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mB, mB2, p, s);
+        case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mb, p, s);
+        case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mb, p, s);
+        case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mb, p, s);
     }
     return fail(FK_EINVAL, "bad tile height");
 }
@@ -653,11 +1000,6 @@ int prepare(const fk_table *t, const TcPack &pk, const int *d_other, const float
     return FK_OK;
 }
 
-const CUtensorMap &map_b(const TcPack &pk, int prec, bool second) {
-    if (prec == FK_TF32) return pk.map_f32;
-    return (second && prec == FK_BF16X3) ? pk.map_lo : pk.map_hi;
-}
-
 template <int PREC>
 int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
     const TcLayout &L = t->tc;
@@ -672,7 +1014,7 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     p.ldo = ldo;
     p.Fm = Fm;
     p.O = O;
-    return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, map_b(L.fwd, PREC, false), map_b(L.fwd, PREC, true), p, s);
+    return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, L.fwd, p, s);
 }
 
 // Adjoint: term 1 (derivative with respect to the first flavour of each
@@ -706,8 +1048,7 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
         p.ldo = ldgo;
         p.gO = gO;
         p.P = parts[k];
-        rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, map_b(*packs[k], PREC, false), map_b(*packs[k], PREC, true),
-                                         p, s);
+        rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, *packs[k], p, s);
         if (rc) return rc;
     }
     const long long n = (long long)R * NFL * t->nxg;
@@ -810,6 +1151,10 @@ int tc_build(fk_table *t, const double *host_fk) {
         if (want_hi && (rc = make_map(&pk->map_hi, pk->hi, 2, pk->ktot_pad, rows, L.n_rows))) return rc;
         if (want_lo && (rc = make_map(&pk->map_lo, pk->lo, 2, pk->ktot_pad, rows, L.n_rows))) return rc;
         if (want_f32 && (rc = make_map(&pk->map_f32, pk->f32, 4, pk->ktot_pad, rows, L.n_rows))) return rc;
+        const int h = L.n_rows / 2;  // a multiple of 8 rows: whole 1024-byte swizzle atoms
+        if (want_hi && (rc = make_map(&pk->half_hi, pk->hi, 2, pk->ktot_pad, rows, h))) return rc;
+        if (want_lo && (rc = make_map(&pk->half_lo, pk->lo, 2, pk->ktot_pad, rows, h))) return rc;
+        if (want_f32 && (rc = make_map(&pk->half_f32, pk->f32, 4, pk->ktot_pad, rows, h))) return rc;
     }
     return FK_OK;
 }

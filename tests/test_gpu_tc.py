@@ -96,6 +96,23 @@ def test_tc_replica_independent_of_batch(prec):
     assert np.array_equal(full[200:201], one)
 
 
+@pytest.mark.parametrize("prec", TC)
+def test_tc_pair_launch_matches_single(prec):
+    """An even number of replica tiles runs on CTA pairs (256-row MMAs over two
+    SMs), an odd number on single CTAs: every replica's result is bit-identical."""
+    t, F = W.config1(R=1024)
+    tab = fk.Table.from_workload(t, precs=(prec,))
+    pair = run(tab, F, prec)               # 8 replica tiles: pairs
+    single = run(tab, F[128:512], prec)    # 3 replica tiles: single CTAs
+    assert np.array_equal(pair[128:512], single)
+    O_ref, S = oracle.had(t, F[:64])
+    assert (np.abs(pair[:64] - O_ref) / S).max() <= BOUND[prec]
+    gO = np.random.default_rng(5).standard_normal((1024, t.fk.shape[0]))
+    g_pair = run_bwd(tab, F[:256], gO[:256], prec)
+    g_single = run_bwd(tab, F[:128], gO[:128], prec)
+    assert np.array_equal(g_pair[:128], g_single)
+
+
 def test_tc_shared_grid_and_ldo():
     """Tables on subsets of a master grid, written into one wide output."""
     g = W.config3(R=130, scale=0.05)

@@ -39,6 +39,12 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--phases", action="store_true",
+                    help="fit case: run the step as three separate phases (per-phase timing) "
+                         "instead of the pipelined per-table chains")
+    ap.add_argument("--waves", type=int, default=1, help="fit case: forward waves of the pipelined step")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="fit case: streams the tables are spread over (0: one per table)")
     ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
                          "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
@@ -209,7 +215,8 @@ ESZ = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4, "tf32": 4}  # table bytes p
 
 
 def roofline(fit, seg, prec):
-    """Roofline entry for the phase that takes longest.
+    """Roofline entry for the pipelined step as a whole, or (phase-separated
+    step) for the phase that takes longest.
 
     Algorithmic bytes of a convolution phase: every table element streamed
     once in the mode's storage (BF16 hi+lo: 4 B; DIS tables in the reduced
@@ -221,8 +228,18 @@ def roofline(fit, seg, prec):
     pk, src = peaks()
     dom = max(seg, key=seg.get)
     t = seg[dom] * 1e-3
-    flops = fit.flops[dom]
     tc = prec in ("bf16", "bf16x3", "tf32")
+    if dom == "step":
+        # pipelined: the phases overlap; every table is streamed once by the
+        # forward and once by the adjoint within the step
+        flops = sum(fit.flops.values())
+        byts = 2 * (fit.elems["had"] * ESZ[prec] + fit.elems["dis"] * ESZ["fp32" if tc else prec])
+        ach = byts / t / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None,
+                "kernel": "whole pipelined step (forward, FP64 chi^2 and adjoint overlapped)",
+                "algorithmic_bytes": byts, "algorithmic_flops": flops, "peak_source": src}
+    flops = fit.flops[dom]
     if dom == "loss":
         peak = 148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         return {"bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -468,7 +485,8 @@ def main():
     del tabs64
     cov = W.covariance(o_true, SEED)
     D = np.concatenate(W.pseudo_data(o_true, SEED))
-    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec)
+    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
+                    pipelined=not args.phases, waves=args.waves)
     fit.capture()
     launches = fit.launches_per_step()
     stream = torch.cuda.current_stream()
@@ -527,7 +545,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16",
                                            "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
-            "data": "synthetic", "config": config_dict(g, args.prec), "roofline": roof,
+            "data": "synthetic", "config": dict(config_dict(g, args.prec), streams=fit.nstreams,
+                                               schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves"),
+            "roofline": roof,
             "e2e": {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": F_host.numel() * F_host.element_size(),
                     "d2h_bytes_per_step": chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size()},

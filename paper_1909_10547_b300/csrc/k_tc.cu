@@ -859,6 +859,11 @@ int opt_in_smem(K kernel, size_t bytes) {
     std::lock_guard<std::mutex> lock(mu);
     if (done.count((const void *)kernel)) return FK_OK;
     FK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    // run with the largest shared-memory carveout: the SM then keeps room
+    // beside the tensor-core CTA for the small CUDA-core kernels (chi^2,
+    // packing, DIS) of concurrent streams
+    FK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     done.insert((const void *)kernel);
     return FK_OK;
 }

@@ -3,17 +3,26 @@
 The step is the hot path of the paper's fit (Sec. 2: gradient descent; Sec. 3:
 the convolution is the most time-consuming operation):
 
-  forward   O[:, off_k : off_k + n_k] = conv(table_k, F)   for every dataset k
-  loss      chi2[r] = (O_r - D)^T C^{-1} (O_r - D),  gO = d chi2 / d O  (FP64)
-  backward  gF = sum_k conv_backward(table_k, F, gO[:, off_k : off_k + n_k])
+  forward   O_k = conv(table_k, F)                      for every dataset k
+  loss      chi2_k[r] = (O_k,r - D_k)^T C_k^{-1} (O_k,r - D_k),  gO_k = d chi2_k / d O_k
+  backward  gF = sum_k conv_backward(table_k, F, gO_k)
+  chi2      = sum_k chi2_k
 
-All three run in libfk.so kernels.  The tables are spread over `nstreams`
-CUDA streams (balanced by their work) so that small tables run side by side
-on the 148 SMs: in the forward each table writes its own columns of O; in the
-backward each stream accumulates into its own gradient buffer and
-fk_grad_sum adds the buffers in a fixed order, so the result does not depend
-on how the streams interleave.  capture() records each phase in a CUDA graph
-(the streams become parallel branches), so a step costs three graph launches.
+The covariance is block diagonal with one block per dataset, so the three
+stages of dataset k depend only on each other.  All run in libfk.so kernels.
+
+pipelined=True (default): each table's chain forward -> chi^2 block ->
+adjoint runs on its own CUDA stream, so the FP64 chi^2 of one dataset
+overlaps the tensor-core and CUDA-core convolutions of the others; the
+per-stream gradient buffers and the per-dataset chi^2 values are then added
+by fk_grad_sum in a fixed order.  capture() records the step as one CUDA
+graph whose streams are parallel branches.
+
+pipelined=False: three phases (all forwards, one chi^2 launch over all
+blocks, all adjoints), each its own graph, for per-phase timing.
+
+Either way the result does not depend on how the streams interleave: every
+table writes its own outputs and every sum runs in a fixed order.
 """
 import numpy as np
 import torch
@@ -25,7 +34,7 @@ NFL = 14
 
 class GlobalFit:
     def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda",
-                 nstreams=8):
+                 nstreams=None, pipelined=True, waves=1):
         """tables: workloads.DisTable/HadTable list sharing one x grid;
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
@@ -47,14 +56,27 @@ class GlobalFit:
         self.R = F.shape[0]
         self.nxg = F.shape[2]
         self.io = io
-        self.cov = Cov(cov_blocks)
-        assert self.cov.n == self.ntot
+        self.pipelined = pipelined
         self.D = torch.tensor(np.asarray(D, np.float64), device=device)
         self.F = torch.tensor(np.asarray(F), dtype=io, device=device)
-        self.O = torch.empty((self.R, self.ntot), dtype=io, device=device)
-        self.gO = torch.empty_like(self.O)
         self.gF = torch.empty_like(self.F)
         self.chi2 = torch.empty(self.R, dtype=torch.float64, device=device)
+        if pipelined:
+            # per dataset: its covariance block, and O_k, gO_k as contiguous
+            # [R][n_k] blocks of one buffer
+            self.covs = [Cov([b]) for b in cov_blocks]
+            assert sum(c.n for c in self.covs) == self.ntot
+            self.Obuf = torch.empty(self.R * self.ntot, dtype=io, device=device)
+            self.gObuf = torch.empty_like(self.Obuf)
+            self.Ok = [self.Obuf[self.R * a:self.R * b].view(self.R, b - a) for a, b in zip(self.offs, self.offs[1:])]
+            self.gOk = [self.gObuf[self.R * a:self.R * b].view(self.R, b - a) for a, b in zip(self.offs, self.offs[1:])]
+            self.Dk = [self.D[a:b] for a, b in zip(self.offs, self.offs[1:])]
+            self.chi2_parts = torch.empty((len(tables), self.R), dtype=torch.float64, device=device)
+        else:
+            self.cov = Cov(cov_blocks)
+            assert self.cov.n == self.ntot
+            self.O = torch.empty((self.R, self.ntot), dtype=io, device=device)
+            self.gO = torch.empty_like(self.O)
         self.graphs = None
         # algorithmic work per step (multiply-adds counted as 2 flops) and the
         # table elements each phase streams
@@ -75,14 +97,22 @@ class GlobalFit:
             work.append(e)
         self.flops = {"forward": fwd, "loss": 2 * int(sum(n * n for n in nd)) * self.R, "backward": bwd}
         # streams: greedy assignment of tables (largest first) to the least
-        # loaded stream
-        self.nstreams = max(1, min(nstreams, len(tables)))
+        # loaded stream; by default one stream per table (up to the 64
+        # gradient parts that grad_sum combines), so that the small per-table
+        # launches overlap
+        self.nstreams = max(1, min(nstreams or 64, len(tables), 64))
         load = [0] * self.nstreams
         self.groups = [[] for _ in range(self.nstreams)]
         for k in sorted(range(len(tables)), key=lambda k: -work[k]):
             s = int(np.argmin(load))
             self.groups[s].append(k)
             load[s] += work[k]
+        # waves of the pipelined step: tables by decreasing work, dealt
+        # round-robin (so each wave has a similar share of the work)
+        self.waves = max(1, int(waves))
+        order = sorted(range(len(tables)), key=lambda k: -work[k])
+        self.wave_tables = [order[w::self.waves] for w in range(self.waves)]
+        self.stream_of = {k: s for s, grp in enumerate(self.groups) for k in grp}
         for grp in self.groups:
             grp.sort()
         self.streams = [torch.cuda.Stream(device=device) for _ in range(self.nstreams)]
@@ -124,23 +154,80 @@ class GlobalFit:
         self._fan_out(body)
         grad_sum([self.gF_parts[s] for s in range(self.nstreams) if self.groups[s]], self.gF)
 
+    def chain(self):
+        """The pipelined step: per stream, forward -> chi^2 -> adjoint of each
+        of its tables, then the fixed-order sums.
+
+        With one stream per table the forwards are also staged in waves:
+        the forwards of wave w start when those of wave w-1 are done, so the
+        FP64 chi^2 (and then the adjoint) of one wave runs while the next
+        wave's forwards occupy the tensor cores, instead of every forward
+        competing at once and every chi^2 waiting for all of them."""
+        if self.nstreams < len(self.tabs) or self.waves <= 1:
+            def body(s):
+                for n, k in enumerate(self.groups[s]):
+                    self._table_chain(s, k, accumulate=n > 0)
+            self._fan_out(body)
+        else:
+            main = torch.cuda.current_stream()
+            start = torch.cuda.Event()
+            start.record(main)
+            ends, prev = [], []
+            for wave in self.wave_tables:
+                done = []
+                for k in wave:
+                    s = self.stream_of[k]
+                    st = self.streams[s]
+                    st.wait_event(start)
+                    for e in prev:
+                        st.wait_event(e)
+                    with torch.cuda.stream(st):
+                        ev = self._table_chain(s, k, accumulate=False)
+                        done.append(ev)
+                        e = torch.cuda.Event()
+                        e.record(st)
+                        ends.append(e)
+                prev = done
+            for e in ends:
+                main.wait_event(e)
+        grad_sum([self.gF_parts[s] for s in range(self.nstreams) if self.groups[s]], self.gF)
+        parts = list(self.chi2_parts)
+        for i in range(0, len(parts), 64):  # fk_grad_sum adds up to 64 parts per call
+            grad_sum(parts[i:i + 64], self.chi2, accumulate=i > 0)
+
+    def _table_chain(self, s, k, accumulate):
+        """forward -> chi^2 -> adjoint of table k on the current stream;
+        returns an event recorded after the forward."""
+        conv(self.tabs[k], self.F, self.tprec[k], out=self.Ok[k])
+        fwd = torch.cuda.Event()
+        fwd.record(torch.cuda.current_stream())
+        chi2(self.covs[k], self.Ok[k], self.Dk[k], grad=True, out=self.chi2_parts[k], gO=self.gOk[k])
+        conv_backward(self.tabs[k], self.F, self.gOk[k], self.tprec[k], gF=self.gF_parts[s],
+                      accumulate=accumulate)
+        return fwd
+
+    def phases(self):
+        """(name, callable) of the step's graph(s), in order."""
+        if self.pipelined:
+            return (("step", self.chain),)
+        return (("forward", self.forward), ("loss", self.loss), ("backward", self.backward))
+
     def step(self):
         if self.graphs is not None:
             for g in self.graphs.values():
                 g.replay()
         else:
-            self.forward()
-            self.loss()
-            self.backward()
+            for _, fn in self.phases():
+                fn()
 
     def capture(self):
-        """Records the three phases in CUDA graphs (after one eager step)."""
-        self.forward()
-        self.loss()
-        self.backward()
+        """Records the step in CUDA graphs (after one eager step): one graph
+        when pipelined, else one per phase."""
+        for _, fn in self.phases():
+            fn()
         torch.cuda.synchronize()
         graphs = {}
-        for name, fn in (("forward", self.forward), ("loss", self.loss), ("backward", self.backward)):
+        for name, fn in self.phases():
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
                 fn()

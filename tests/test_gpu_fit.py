@@ -5,7 +5,9 @@ dchi2/df_a(x_i).  Checks: (1) FKConv.backward equals the oracle gradient;
 (2) the fit step's gradient equals the oracle chain (oracle forward, oracle
 chi^2 gradient, oracle adjoint); (3) it matches central finite differences of
 the GPU chi^2 with h = 1e-6 (absolute, FP64) on sampled coordinates and random
-directions, to 1e-6 of max(|g.v|, 1e-3 |g|).
+directions, to 1e-6 of max(|g.v|, 1e-3 |g|); (4) the pipelined and the
+phase-separated schedules agree with the oracle and replay bit-exactly from
+their graphs.
 """
 import numpy as np
 import pytest
@@ -58,9 +60,11 @@ def test_autograd_matches_oracle_gradient(prec):
     assert np.all(np.abs(Fd.grad.double().cpu().numpy() - ref) <= tol * a)
 
 
-def test_fit_step_gradient_matches_oracle_chain(small_global):
+@pytest.mark.parametrize("pipelined", [True, False])
+def test_fit_step_gradient_matches_oracle_chain(small_global, pipelined):
+    """Both schedules: per-table chains on parallel streams, and three phases."""
     g, cov, D = small_global
-    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp64")
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp64", pipelined=pipelined)
     fit.step()
     torch.cuda.synchronize()
     chi_ref, gF_ref = oracle_chain(g, cov, D, g.F)
@@ -82,8 +86,7 @@ def test_fit_step_gradient_finite_differences(small_global):
 
     def chi2_at(F):
         fit.F.copy_(torch.tensor(F, device="cuda"))
-        fit.forward()
-        fit.loss()
+        fit.step()
         torch.cuda.synchronize()
         return fit.chi2.cpu().numpy().copy()
 
@@ -121,9 +124,10 @@ def test_fit_step_reduced_precision_chi2(small_global, prec, tol):
     assert rel.max() <= tol
 
 
-def test_graph_capture_replays_the_step(small_global):
+@pytest.mark.parametrize("pipelined", [True, False])
+def test_graph_capture_replays_the_step(small_global, pipelined):
     g, cov, D = small_global
-    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp32")
+    fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="fp32", pipelined=pipelined)
     fit.step()
     torch.cuda.synchronize()
     chi_eager = fit.chi2.cpu().numpy().copy()

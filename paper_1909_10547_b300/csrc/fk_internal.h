@@ -75,6 +75,12 @@ struct TcPack {
     __nv_bfloat16 *hi = nullptr;  // BF16 / hi part
     __nv_bfloat16 *lo = nullptr;  // lo part (BF16X3)
     float *f32 = nullptr;         // TF32 operand (FP32 bits, rounded)
+    // A-operand gather maps (device): kmeta[k] = offset o * nx_grid + xmap[j]
+    // of the PDF value f_o(x_j) in one replica's F row for K column k (o the
+    // channel's other flavour), or -1 for padding; mmeta[g * nx + i] = offset
+    // of f_{a_g}(x_i), the forward epilogue multiplier
+    int *kmeta = nullptr;
+    int *mmeta = nullptr;
     CUtensorMap map_hi;   // (the type is 128-byte aligned)
     CUtensorMap map_lo;
     CUtensorMap map_f32;
@@ -88,6 +94,7 @@ struct TcLayout {
     int ntile_n = 0;    // ceil(ndata / G)
     int n_rows = 0;     // MMA N = G * nx rounded up to 16
     TcPack fwd, bwd;
+    int8_t *gmap = nullptr;  // device [2][14]: group of flavour a in fwd / bwd packing, or -1
 };
 
 }  // namespace fk

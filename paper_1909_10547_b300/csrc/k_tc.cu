@@ -709,38 +709,67 @@ __device__ __forceinline__ int group_of(const TcGroups &gr, int k) {
     return -1;
 }
 
+// stores 8 consecutive operand values at element index at (a multiple of 8)
+template <int PREC>
+__device__ __forceinline__ void store8(size_t at, const float (&v)[8], __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                       float *f32) {
+    if (PREC == FK_TF32) {
+        float4 a, b;
+        a.x = tf32_rna(v[0]);
+        a.y = tf32_rna(v[1]);
+        a.z = tf32_rna(v[2]);
+        a.w = tf32_rna(v[3]);
+        b.x = tf32_rna(v[4]);
+        b.y = tf32_rna(v[5]);
+        b.z = tf32_rna(v[6]);
+        b.w = tf32_rna(v[7]);
+        reinterpret_cast<float4 *>(f32 + at)[0] = a;
+        reinterpret_cast<float4 *>(f32 + at)[1] = b;
+    } else {
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            h[u] = __float2bfloat16_rn(v[u]);
+            l[u] = __float2bfloat16_rn(v[u] - __bfloat162float(h[u]));
+        }
+        *reinterpret_cast<uint4 *>(hi + at) = *reinterpret_cast<const uint4 *>(h);
+        if (PREC == FK_BF16X3) *reinterpret_cast<uint4 *>(lo + at) = *reinterpret_cast<const uint4 *>(l);
+    }
+}
+
 // A operand A[r][k] = f^r_{o_c}(x_j) for k = (channel c of its group, j), where
 // o_c is the channel's other flavour (b_c for the forward packing, a_c for the
-// transposed one), and, if Fm is not NULL, the forward epilogue multipliers
-// Fm[g][i][r] = f^r_{a_g}(x_i).
+// transposed one), gathered through kmeta.  Grid (ceil(ktot_pad / 2048),
+// min(R_pad, 65535)), rows r strided by the grid height: 8 consecutive K
+// columns per thread, one 16-byte store per operand copy (ktot_pad is a
+// multiple of 64).
 template <int PREC>
-__global__ void k_pack_pdf(const TcGroups gr, const int *__restrict__ cb, const int *__restrict__ xmap,
-                           int nx, int nxg, const float *__restrict__ F, int R, int R_pad, int ktot_pad,
-                           __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32, float *__restrict__ Fm) {
-    const long long nA = (long long)R_pad * ktot_pad;
-    const long long nM = Fm ? (long long)gr.ngroups * nx * R_pad : 0;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nA + nM;
-         idx += (long long)gridDim.x * blockDim.x) {
-        if (idx < nA) {
-            const int r = (int)(idx / ktot_pad), k = (int)(idx % ktot_pad);
-            float v = 0.f;
-            const int g = group_of(gr, k);
-            if (r < R && g >= 0) {
-                const int q = (k - gr.kbeg[g]) / nx, j = (k - gr.kbeg[g]) % nx;
-                if (q < gr.nch[g]) {
-                    const int c = gr.chan[gr.ch0[g] + q];
-                    v = F[((size_t)r * NFL + cb[c]) * nxg + xmap[j]];
-                }
-            }
-            store_op<PREC>(idx, v, hi, lo, f32);
-        } else {
-            const long long m = idx - nA;
-            const int r = (int)(m % R_pad);
-            const int i = (int)((m / R_pad) % nx);
-            const int g = (int)(m / ((long long)R_pad * nx));
-            Fm[m] = r < R ? F[((size_t)r * NFL + gr.flav[g]) * nxg + xmap[i]] : 0.f;
-        }
+__global__ void __launch_bounds__(256) k_pack_pdf(const int *__restrict__ kmeta, int ktot_pad,
+                                                  const float *__restrict__ F, int frow, int R, int R_pad,
+                                                  __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+    const int k0 = (blockIdx.x * 256 + threadIdx.x) * 8;
+    if (k0 >= ktot_pad) return;
+    int o[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) o[u] = __ldg(kmeta + k0 + u);
+    for (int r = blockIdx.y; r < R_pad; r += gridDim.y) {
+        const float *Fr = F + (size_t)r * frow;
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = (r < R && o[u] >= 0) ? __ldg(Fr + o[u]) : 0.f;
+        store8<PREC>((size_t)r * ktot_pad + k0, v, hi, lo, f32);
     }
+}
+
+// Forward epilogue multipliers Fm[m][r] = f^r(mmeta[m]), m = g * nx + i (the
+// value f^r_{a_g}(x_i)); zero for padding replicas.  Grid (nm, ceil(R_pad / 256)).
+__global__ void __launch_bounds__(256) k_pack_fm(const int *__restrict__ mmeta, const float *__restrict__ F,
+                                                 int frow, int R, int R_pad, float *__restrict__ Fm) {
+    const int m = blockIdx.x;
+    const int r = blockIdx.y * 256 + threadIdx.x;
+    if (r >= R_pad) return;
+    const int o = __ldg(mmeta + m);
+    Fm[(size_t)m * R_pad + r] = r < R ? __ldg(F + (size_t)r * frow + o) : 0.f;
 }
 
 // B operand from the FP64 table [ndata][nc][nx][nx]: row nt * n_rows + u * G + dl
@@ -775,23 +804,41 @@ __global__ void k_pack_table(const TcGroups gr, const double *__restrict__ fk, i
 
 // Adjoint gather: gF[r][a][m] (+)= sum_t P1[t][g1(a)][i(m)][r] + sum_t P2[t][g2(a)][i(m)][r]
 // with i(m) the table's x index of grid point m, g1/g2 the groups of flavour a
-// in the forward and transposed packings (-1: none); tiles t in order.
-__global__ void k_adj_gather(const float *__restrict__ P1, const float *__restrict__ P2, int ntile,
-                             int ng1, int ng2, const int8_t *__restrict__ g1, const int8_t *__restrict__ g2,
-                             const int *__restrict__ xinv, int nx, int nxg, int R, int R_pad,
-                             int accumulate, float *__restrict__ gF) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)R * NFL * nxg) return;
-    const int r = (int)(idx % R);
-    const int m = (int)((idx / R) % nxg);
-    const int a = (int)(idx / ((long long)R * nxg));
-    const int i = xinv[m];
+// in the forward and transposed packings (-1: none).  Grid (ceil(R / 128),
+// nxg, 14): one (a, m) per block row, replicas across threads.  Each sum over
+// tiles runs as four interleaved partial sums (t mod 4) added in a fixed
+// order, so the loads of four tiles are in flight at once.
+__global__ void __launch_bounds__(128) k_adj_gather(const float *__restrict__ P1, const float *__restrict__ P2,
+                                                    int ntile, int ng1, int ng2, const int8_t *__restrict__ g1,
+                                                    const int8_t *__restrict__ g2, const int *__restrict__ xinv,
+                                                    int nx, int nxg, int R, int R_pad, int accumulate,
+                                                    float *__restrict__ gF) {
+    const int r = blockIdx.x * 128 + threadIdx.x;
+    const int m = blockIdx.y, a = blockIdx.z;
+    if (r >= R) return;
+    const int i = __ldg(xinv + m);
     float s = 0.f;
     if (i >= 0) {
-        if (g1[a] >= 0)
-            for (int t = 0; t < ntile; ++t) s += P1[(((size_t)t * ng1 + g1[a]) * nx + i) * R_pad + r];
-        if (g2[a] >= 0)
-            for (int t = 0; t < ntile; ++t) s += P2[(((size_t)t * ng2 + g2[a]) * nx + i) * R_pad + r];
+        const int ga[2] = {__ldg(g1 + a), __ldg(g2 + a)};
+        const int ng[2] = {ng1, ng2};
+        const float *P[2] = {P1, P2};
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            if (ga[pass] < 0) continue;
+            // element (t, g, i, r) at ((t * ng + g) * nx + i) * R_pad + r
+            const size_t step = (size_t)ng[pass] * nx * R_pad;
+            const float *p = P[pass] + ((size_t)ga[pass] * nx + i) * R_pad + r;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int t = 0;
+            for (; t + 4 <= ntile; t += 4) {
+                s0 += __ldg(p + (size_t)t * step);
+                s1 += __ldg(p + (size_t)(t + 1) * step);
+                s2 += __ldg(p + (size_t)(t + 2) * step);
+                s3 += __ldg(p + (size_t)(t + 3) * step);
+            }
+            for (; t < ntile; ++t) s0 += __ldg(p + (size_t)t * step);
+            s += (s0 + s1) + (s2 + s3);
+        }
     }
     const size_t o = ((size_t)r * NFL + a) * nxg + m;
     gF[o] = accumulate ? gF[o] + s : s;
@@ -964,8 +1011,8 @@ int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2
 // Packs the A operand (and, if Fm is not NULL, the forward multipliers) for one
 // packing of the table, builds its tensor maps and fills the common params.
 template <int PREC>
-int prepare(const fk_table *t, const TcPack &pk, const int *d_other, const float *F, int R, Scratch &scr,
-            float *Fm, cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p) {
+int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch &scr, float *Fm,
+            cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p) {
     const TcLayout &L = t->tc;
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
@@ -977,12 +1024,17 @@ int prepare(const fk_table *t, const TcPack &pk, const int *d_other, const float
         FK_CUDA(scr.get(&hi, nA));
         if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
     }
-    const long long n = (long long)nA + (Fm ? (long long)pk.grp.ngroups * t->nx * R_pad : 0);
-    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 8);
-    k_pack_pdf<PREC><<<blocks, 256, 0, s>>>(pk.grp, d_other, t->d_xmap, t->nx, t->nxg, F, R, R_pad,
-                                            pk.ktot_pad, hi, lo, f32, Fm);
+    const int frow = NFL * t->nxg;
+    k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
+                       s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
     count_launch();
     FK_CUDA(cudaGetLastError());
+    if (Fm) {
+        k_pack_fm<<<dim3((unsigned)(pk.grp.ngroups * t->nx), (unsigned)((R_pad + 255) / 256)), 256, 0, s>>>(
+            pk.mmeta, F, frow, R, R_pad, Fm);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
+    }
     const int esz = Tr<PREC>::ESZ;
     int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
     if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);
@@ -1014,7 +1066,7 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     FK_CUDA(scr.get(&Fm, (size_t)L.fwd.grp.ngroups * t->nx * R_pad));
     CUtensorMap mA, mA2;
     TcParams p;
-    int rc = prepare<PREC>(t, L.fwd, t->d_cb, F, R, scr, Fm, s, mA, mA2, p);
+    int rc = prepare<PREC>(t, L.fwd, F, R, scr, Fm, s, mA, mA2, p);
     if (rc) return rc;
     p.ldo = ldo;
     p.Fm = Fm;
@@ -1033,22 +1085,14 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     Scratch scr(s);
     float *P1 = nullptr, *P2 = nullptr;
-    int8_t *gmap = nullptr;
     FK_CUDA(scr.get(&P1, (size_t)L.ntile_n * L.fwd.grp.ngroups * t->nx * R_pad));
     FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
-    FK_CUDA(scr.get(&gmap, 2 * NFL));
-    int8_t hmap[2 * NFL];
-    for (int a = 0; a < 2 * NFL; ++a) hmap[a] = -1;
-    for (int g = 0; g < L.fwd.grp.ngroups; ++g) hmap[L.fwd.grp.flav[g]] = (int8_t)g;
-    for (int g = 0; g < L.bwd.grp.ngroups; ++g) hmap[NFL + L.bwd.grp.flav[g]] = (int8_t)g;
-    FK_CUDA(cudaMemcpyAsync(gmap, hmap, sizeof(hmap), cudaMemcpyHostToDevice, s));
     const TcPack *packs[2] = {&L.fwd, &L.bwd};
-    const int *others[2] = {t->d_cb, t->d_ca};
     float *parts[2] = {P1, P2};
     for (int k = 0; k < 2; ++k) {
         CUtensorMap mA, mA2;
         TcParams p;
-        int rc = prepare<PREC>(t, *packs[k], others[k], F, R, scr, nullptr, s, mA, mA2, p);
+        int rc = prepare<PREC>(t, *packs[k], F, R, scr, nullptr, s, mA, mA2, p);
         if (rc) return rc;
         p.ldo = ldgo;
         p.gO = gO;
@@ -1056,10 +1100,9 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
         rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, *packs[k], p, s);
         if (rc) return rc;
     }
-    const long long n = (long long)R * NFL * t->nxg;
-    k_adj_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P1, P2, L.ntile_n, L.fwd.grp.ngroups,
-                                                             L.bwd.grp.ngroups, gmap, gmap + NFL, t->d_xinv,
-                                                             t->nx, t->nxg, R, R_pad, accumulate, gF);
+    k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(
+        P1, P2, L.ntile_n, L.fwd.grp.ngroups, L.bwd.grp.ngroups, L.gmap, L.gmap + NFL, t->d_xinv, t->nx,
+        t->nxg, R, R_pad, accumulate, gF);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
@@ -1118,6 +1161,35 @@ int tc_build(fk_table *t, const double *host_fk) {
     const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
     const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
     const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
+    // gather maps of the A operand and of the forward multipliers, and the
+    // adjoint gather's flavour -> group maps
+    {
+        const std::vector<int> *other[2] = {&t->cb, &t->ca};
+        TcPack *packs[2] = {&L.fwd, &L.bwd};
+        for (int w = 0; w < 2; ++w) {
+            TcPack &pk = *packs[w];
+            std::vector<int> km(pk.ktot_pad, -1), mm((size_t)pk.grp.ngroups * t->nx);
+            for (int g = 0; g < pk.grp.ngroups; ++g) {
+                for (int q = 0; q < pk.grp.nch[g]; ++q) {
+                    const int c = pk.grp.chan[pk.grp.ch0[g] + q];
+                    for (int j = 0; j < t->nx; ++j)
+                        km[pk.grp.kbeg[g] + q * t->nx + j] = (*other[w])[c] * t->nxg + t->xmap[j];
+                }
+                for (int i = 0; i < t->nx; ++i) mm[(size_t)g * t->nx + i] = pk.grp.flav[g] * t->nxg + t->xmap[i];
+            }
+            if (cudaMalloc(&pk.kmeta, km.size() * sizeof(int)) || cudaMalloc(&pk.mmeta, mm.size() * sizeof(int)))
+                return fail(FK_ENOMEM, "tensor-core gather maps");
+            FK_CUDA(cudaMemcpy(pk.kmeta, km.data(), km.size() * sizeof(int), cudaMemcpyHostToDevice));
+            FK_CUDA(cudaMemcpy(pk.mmeta, mm.data(), mm.size() * sizeof(int), cudaMemcpyHostToDevice));
+            t->bytes += (km.size() + mm.size()) * sizeof(int);
+        }
+        int8_t hmap[2 * NFL];
+        for (int a = 0; a < 2 * NFL; ++a) hmap[a] = -1;
+        for (int g = 0; g < L.fwd.grp.ngroups; ++g) hmap[L.fwd.grp.flav[g]] = (int8_t)g;
+        for (int g = 0; g < L.bwd.grp.ngroups; ++g) hmap[NFL + L.bwd.grp.flav[g]] = (int8_t)g;
+        if (cudaMalloc(&L.gmap, sizeof(hmap))) return fail(FK_ENOMEM, "tensor-core gather maps");
+        FK_CUDA(cudaMemcpy(L.gmap, hmap, sizeof(hmap), cudaMemcpyHostToDevice));
+    }
     for (TcPack *pk : {&L.fwd, &L.bwd}) {
         const size_t elems = (size_t)L.ntile_n * L.n_rows * pk->ktot_pad;
         if ((want_hi && cudaMalloc(&pk->hi, elems * 2)) || (want_lo && cudaMalloc(&pk->lo, elems * 2)) ||
@@ -1190,9 +1262,14 @@ void tc_free(fk_table *t) {
         cudaFree(pk->hi);
         cudaFree(pk->lo);
         cudaFree(pk->f32);
+        cudaFree(pk->kmeta);
+        cudaFree(pk->mmeta);
         pk->hi = pk->lo = nullptr;
         pk->f32 = nullptr;
+        pk->kmeta = pk->mmeta = nullptr;
     }
+    cudaFree(t->tc.gmap);
+    t->tc.gmap = nullptr;
 }
 
 int device_status(int reset) {

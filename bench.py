@@ -13,6 +13,7 @@ of the workload (weak scaling, no collective on the data path); rank 0
 prints one JSON line.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -52,6 +53,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
+    ap.add_argument("--table", default="stress", choices=["stress", "config1"],
+                    help="stress case: the stress table, or the plain hadronic table of configs 1-2 "
+                         "(200 data points, 60 channels, nx = 30; R = 512 is config 2)")
     ap.add_argument("--replicas", type=int, default=1, help="stress case: replicas")
     return ap.parse_args()
 
@@ -275,6 +279,25 @@ def config_dict(g, prec):
             "graphs": True, "parallelism": "replicas only (one independent copy per rank)"}
 
 
+def traffic_of(kernel, prec, ndata, replicas):
+    """DRAM bytes per launch of `kernel` for this stress workload, from the
+    committed ncu capture list (profiles/dram_traffic.txt), or None when no
+    capture matches or the kernel's source has changed since it was taken."""
+    src = {"k_tc": "k_tc.cu", "k_stream": "k_cc.cu"}[kernel]
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "paper_1909_10547_b300", "csrc", src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    try:
+        lines = open(os.path.join(here, "profiles", "dram_traffic.txt")).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        w = ln.split()
+        if len(w) >= 6 and not ln.startswith("#") and w[:5] == [kernel, sha, prec, str(ndata), str(replicas)]:
+            return float(w[5])
+    return None
+
+
 def run_stress(args):
     """One convolution of the stress table, timed over graph replays: the
     kernel-level roofline (HBM for the streaming path at small R, tensor pipe
@@ -282,11 +305,17 @@ def run_stress(args):
     import torch
     import paper_1909_10547_b300 as fk
     from paper_1909_10547_b300 import workloads as W
-    t = W.stress_table(ndata=args.ndata)
-    tab = fk.Table.from_workload(t, precs=(args.prec,))
-    x = W.xgrid(50, 1e-7)
     R = args.replicas
-    F = W.pdf_replicas(x, W.pdf_params(np.random.default_rng(1)), R, np.random.default_rng(2) if R > 1 else None)
+    if args.table == "config1":
+        t, F = W.config1(R=R)
+        args.ndata = t.ndata
+        name = f"plain hadronic table (configs 1-2) 200 x 60 channels x 30 x 30, one convolution, R={R}"
+    else:
+        t = W.stress_table(ndata=args.ndata)
+        x = W.xgrid(50, 1e-7)
+        F = W.pdf_replicas(x, W.pdf_params(np.random.default_rng(1)), R, np.random.default_rng(2) if R > 1 else None)
+        name = f"hadronic stress table {args.ndata} x 196 channels x 50 x 50, one convolution, R={R}"
+    tab = fk.Table.from_workload(t, precs=(args.prec,))
     dt = torch.float64 if args.prec == "fp64" else torch.float32
     Fd = torch.tensor(F, dtype=dt, device="cuda")
     O = fk.conv(tab, Fd, args.prec)
@@ -325,12 +354,15 @@ def run_stress(args):
         roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": ach / tpeak, "traffic": None}
     roof["peak_source"] = src
+    kern = "k_tc" if tc else ("k_stream" if R <= 4 and args.prec in ("fp32", "fp64") else None)
+    if kern:
+        roof["kernel"] = f"{kern} (timed as the whole convolution call, operand packing included)"
+        roof["traffic"] = traffic_of(kern, args.prec, args.ndata, R) if args.table == "stress" else None
     line = {"metric": METRIC, "value": args.ndata * R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": f"hadronic stress table {args.ndata} x 196 channels x 50 x 50, one "
-                                   f"convolution, R={R}", "l2": "table larger than L2" if byts > 126e6 else
-                       "table fits in L2", "graphs": True},
+            "config": {"workload": name, "l2": "table larger than L2" if byts > 126e6 else
+                       "table fits in L2 (warm: replayed back to back)", "graphs": True},
             "roofline": roof, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 

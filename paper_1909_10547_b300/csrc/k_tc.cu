@@ -249,18 +249,24 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem) {
     else
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 64 consecutive accumulator columns of this warp's 32 TMEM lanes (one
+// column per register), waited for inside the same statement so that no use
+// of v can be scheduled before the load has completed.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-          "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-          "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+          "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+          "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+          "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+          "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr)
+        : "memory");
 }
 
 // ------------------------------------------------------------ kernel ----
@@ -609,7 +615,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     acc[dl] = (r < p.R && dd < p.ndata) ? __ldg(p.gO + (size_t)r * p.ldo + dd) : 0.f;
                 }
             }
-            const int ncols = ((G * p.nx + 31) / 32) * 32;
+            const int ncols = G * p.nx;  // accumulator columns in use
             constexpr int MI = 256 / G;  // x points a 256-column accumulator can hold
             for (int g = 0; g < p.ngroups; ++g, ++gc) {
                 const int b = gc & 1;
@@ -632,25 +638,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
                 float *pg = MODE == MODE_ADJ ? p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r : nullptr;
+                // 64 columns per TMEM round trip; columns of x points >= nx
+                // (never written by the MMA) are skipped, not multiplied by 0
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (c * 32 < ncols) {
-                        uint32_t v[32];
-                        tmem_ld32(taddr + (uint32_t)(c * 32), v);
-                        if (MODE == MODE_FWD) {
+                for (int c = 0; c < 4; ++c) {
+                    if (c * 64 < ncols) {
+                        uint32_t v[64];
+                        tmem_ld64(taddr + (uint32_t)(c * 64), v);
 #pragma unroll
-                            for (int u = 0; u < 32 / G; ++u)
+                        for (int u = 0; u < 64 / G; ++u) {
+                            const int i = c * (64 / G) + u;
+                            if (i < p.nx) {
+                                if (MODE == MODE_FWD) {
 #pragma unroll
-                                for (int dl = 0; dl < G; ++dl)
-                                    acc[dl] = fmaf(m[c * (32 / G) + u], __uint_as_float(v[u * G + dl]), acc[dl]);
-                        } else {
+                                    for (int dl = 0; dl < G; ++dl)
+                                        acc[dl] = fmaf(m[i], __uint_as_float(v[u * G + dl]), acc[dl]);
+                                } else {
+                                    float s = 0.f;
 #pragma unroll
-                            for (int u = 0; u < 32 / G; ++u) {
-                                const int i = c * (32 / G) + u;
-                                float s = 0.f;
-#pragma unroll
-                                for (int dl = 0; dl < G; ++dl) s = fmaf(acc[dl], __uint_as_float(v[u * G + dl]), s);
-                                if (i < p.nx) pg[(size_t)i * p.R_pad] = s;
+                                    for (int dl = 0; dl < G; ++dl) s = fmaf(acc[dl], __uint_as_float(v[u * G + dl]), s);
+                                    pg[(size_t)i * p.R_pad] = s;
+                                }
                             }
                         }
                     }

@@ -159,10 +159,10 @@ int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
  * driver).  Arguments, layouts and results are those of fk_had_conv.
  *  - Temporary partial sums go to one static device array of 8 MiB that every
  *    GPU loading this library reserves until the process exits.  A call whose
- *    partial sums do not fit (roughly R * ndata * ceil(E / 4096) values for
- *    R <= 4, R * ndata * min(nc, ~300 / ceil(ndata / 64)) values otherwise, of
- *    8 or 4 bytes; E = nc * nx * nx) returns FK_EINVAL and says how many bytes
- *    it needed; split the replicas over several calls.
+ *    partial sums do not fit (roughly ndata * ceil(E / 4096) values for R = 1,
+ *    R * ndata * min(nc, ~300 / ceil(ndata / 128)) values otherwise, of 8 or
+ *    4 bytes; E = nc * nx * nx) returns FK_EINVAL and says how many bytes it
+ *    needed; split the replicas over several calls.
  *  - The first call on each device looks up the array's device address (a
  *    one-time set-up); make that first call before any stream capture.
  *  - All calls share the array and nothing is carried from one call to the

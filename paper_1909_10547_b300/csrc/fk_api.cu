@@ -206,7 +206,11 @@ int fk_version(void) { return 100; }
 
 uint64_t fk_kernel_launches(void) { return g_launches.load(); }
 
-int fk_device_status(int reset) { return device_status(reset); }
+int fk_device_status(int reset) {
+    const int a = device_status(reset);
+    const int b = cc_device_status(reset);
+    return a != FK_OK ? a : b;
+}
 
 int fk_table_create_dis(const double *fk, int ndata, const int *flav, int nflav, int nx,
                         const int *xmap, int nx_grid, unsigned prec_mask, fk_table **out) {

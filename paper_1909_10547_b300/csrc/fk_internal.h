@@ -142,7 +142,14 @@ int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, 
            int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);
 // FK_ETIMEDOUT if a kernel's bounded wait ran out since the last reset
+// (device_status: tensor-core kernels; cc_device_status: CUDA-core kernels)
 int device_status(int reset);
+int cc_device_status(int reset);
+// 2-D tensor map over a row-major [rows][cols] array of esz-byte (4 or 8)
+// floating-point elements, boxes of box_cols x box_rows, no swizzle,
+// zero-filled outside the array (k_tc.cu)
+int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_cols,
+                   int box_rows);
 // conversion helpers (k_cc.cu)
 int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
                  float *d32, cudaStream_t s);

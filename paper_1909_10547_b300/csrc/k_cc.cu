@@ -23,6 +23,9 @@
 #include <set>
 
 namespace fk {
+
+__device__ int g_fk_cc_error;  // non-zero after a bounded wait of k_fac ran out
+
 namespace {
 
 template <typename T>
@@ -301,6 +304,228 @@ __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict_
 }
 
 // ----------------------------------------------------------------------------
+// Factorised many-replica kernel (hadronic, R >= 2).  Eq. 1 per channel c and
+// x point x_i of its first flavour:
+//   O[d][r] = sum_c sum_i f_{a_c}(x_i)[r] * Y_ci[d][r],
+//   Y_ci[d][r] = sum_j FK[d][c][i][j] f_{b_c}(x_j)[r].
+// A CTA owns FAC_TDT data points x TRT replicas and the channels of its split.
+// Y is a register-blocked product (each thread TM data points x TN replicas,
+// K = the nx points x_j).  The FK rows of step (c, i) arrive by one TMA copy
+// of a FAC_TDT x W box (W >= nx + the 16-byte alignment remainder), double
+// buffered on two mbarriers so that the next step's copy overlaps this step's
+// products; the two PDF columns of the channel are staged once per channel.
+// The table is read once per replica tile.
+// grid (ceil(ndata / FAC_TDT), ceil(R / TRT), nsplit);
+// part[(split * R + r) * ndata + d] as for k_tile.
+// ----------------------------------------------------------------------------
+constexpr int FAC_TDT = 128;
+
+template <typename T, int TRT>
+struct FacCfg {
+    static constexpr int TN = sizeof(T) == 4 ? 4 : 2;  // replicas per thread
+    static constexpr int RT = TRT / TN;                 // threads along replicas
+    static constexpr int DT = 256 / RT;                 // threads along data points
+    static constexpr int TM = FAC_TDT / DT;             // data points per thread: td + m * DT
+    static_assert(RT * DT == 256 && TM * DT == FAC_TDT, "tile shape");
+};
+
+// Box width W of the staged rows: covers nx elements from any start, is a
+// multiple of 16 bytes (a TMA box row), and W = 4 (mod 8) so that the rows
+// td, td+1, ... a warp reads at one x_j fall in different banks.
+__host__ __device__ constexpr int fac_width(int nx, int esz) {
+    const int e16 = 16 / esz;
+    int w = nx + e16 - 1;
+    w = (w + e16 - 1) / e16 * e16;
+    while (w % 8 != 4) w += e16;
+    return w;
+}
+
+template <typename T, int TRT>
+size_t fac_smem(int nx) {
+    // 1024 for alignment of the TMA destination, two boxes, two PDF columns
+    return 1024 + sizeof(T) * (2 * (size_t)FAC_TDT * fac_width(nx, sizeof(T)) + 2 * (size_t)nx * TRT);
+}
+
+// N consecutive values from shared memory in 16-byte loads
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T *p, T (&v)[N]) {
+    static_assert((N * sizeof(T)) % 16 == 0, "16-byte multiples");
+#pragma unroll
+    for (int k = 0; k < N * (int)sizeof(T) / 16; ++k) {
+        const float4 q = reinterpret_cast<const float4 *>(p)[k];
+        memcpy(&v[k * 16 / sizeof(T)], &q, 16);
+    }
+}
+
+// 2 s per wait; a thread whose wait ran out stops waiting (dead) and raises
+// g_fk_cc_error, read by fk_device_status
+constexpr unsigned long long FAC_WAIT_NS = 2000000000ull;
+__device__ __forceinline__ unsigned long long cc_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool cc_mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+template <typename T, int TRT>
+__global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap map, TableView tv,
+                                             const T *__restrict__ F, int R, int nsplit,
+                                             T *__restrict__ part) {
+    using C = FacCfg<T, TRT>;
+    constexpr int TM = C::TM, TN = C::TN, E16 = 16 / (int)sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    const int nx = tv.nx, W = fac_width(nx, sizeof(T));
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t abase = (raw + 1023u) & ~1023u;
+    T *As = reinterpret_cast<T *>(smem_raw + (abase - raw));  // [2][FAC_TDT][W]
+    T *Fa = As + 2 * FAC_TDT * W;                                // [nx][TRT]
+    T *Fb = Fa + nx * TRT;                                       // [nx][TRT]
+    const uint32_t box_bytes = (uint32_t)(FAC_TDT * W * sizeof(T));
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+
+    const int d0 = blockIdx.x * FAC_TDT, r0 = blockIdx.y * TRT, sp = blockIdx.z;
+    const int tr = threadIdx.x % C::RT, td = threadIdx.x / C::RT;
+    const int c_b = (int)((long long)tv.nch * sp / nsplit);
+    const int c_e = (int)((long long)tv.nch * (sp + 1) / nsplit);
+    const int nsteps = (c_e - c_b) * nx;
+    const size_t fstride = (size_t)NFL * tv.nxg;
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map) : "memory");
+    }
+    __syncthreads();
+    // first K element of step s, rounded down to 16 bytes (the box origin)
+    auto step_off = [&](int s_) {
+        const int c = c_b + s_ / nx, i = s_ - (s_ / nx) * nx;
+        return ((long long)c * nx + i) * nx;
+    };
+    // thread 0: copy the rows of step s into buffer buf
+    auto stage = [&](int s_, int buf) {
+        const long long off = step_off(s_);
+        const int x0 = (int)(off - off % E16);
+        const uint32_t bar = bar0 + 8u * buf;
+        const uint32_t dst = abase + (uint32_t)buf * box_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(box_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+            "l"((uint64_t)&map), "r"(bar), "r"(x0), "r"(d0)
+            : "memory");
+    };
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int n = 0; n < TN; ++n) acc[m][n] = T(0);
+
+    bool dead = false;
+    int issued = 0;  // copies issued by thread 0
+    if (threadIdx.x == 0 && nsteps > 0) {
+        stage(0, 0);
+        issued = 1;
+    }
+    int cur_c = -1;
+    for (int s_ = 0; s_ < nsteps; ++s_) {
+        const int buf = s_ & 1;
+        const int c = c_b + s_ / nx, i = s_ - (s_ / nx) * nx;
+        if (c != cur_c) {
+            // new channel: its two PDF columns (every thread is past the
+            // previous channel's last step: the barrier that ended it)
+            const int fa = tv.ca[c], fb = tv.cb[c];
+            for (int idx = threadIdx.x; idx < nx * TRT; idx += 256) {
+                const int k = idx / TRT, rr = idx - k * TRT;
+                const int r = r0 + rr;
+                T va = T(0), vb = T(0);
+                if (r < R) {
+                    const T *Fr = F + (size_t)r * fstride;
+                    const int m = tv.xmap[k];
+                    va = Fr[fa * tv.nxg + m];
+                    vb = Fr[fb * tv.nxg + m];
+                }
+                Fa[idx] = va;
+                Fb[idx] = vb;
+            }
+            cur_c = c;
+        }
+        // the next step's box streams in while this step computes (its
+        // buffer was released by the barrier that ended the previous step)
+        if (threadIdx.x == 0 && s_ + 1 < nsteps && !dead) {
+            stage(s_ + 1, buf ^ 1);
+            ++issued;
+        }
+        __syncthreads();  // Fa/Fb written
+        // wait for this step's box (phase s/2 of its buffer's barrier)
+        if (!dead && !cc_mbar_try(bar0 + 8u * buf, (uint32_t)(s_ >> 1) & 1u)) {
+            const unsigned long long t0 = cc_gtimer();
+            while (!cc_mbar_try(bar0 + 8u * buf, (uint32_t)(s_ >> 1) & 1u)) {
+                if (cc_gtimer() - t0 > FAC_WAIT_NS) {
+                    dead = true;
+                    atomicExch(&g_fk_cc_error, 1);
+                    break;
+                }
+            }
+        }
+        if (!dead) {
+            const int rem = (int)(step_off(s_) % E16);
+            const T *A = As + buf * FAC_TDT * W + td * W + rem;
+            const T *B = Fb + tr * TN;
+            T y[TM][TN];
+#pragma unroll
+            for (int m = 0; m < TM; ++m)
+#pragma unroll
+                for (int n = 0; n < TN; ++n) y[m][n] = T(0);
+#pragma unroll 2
+            for (int j = 0; j < nx; ++j) {
+                T a[TM], b[TN];
+                lds_vec<T, TN>(B + j * TRT, b);
+#pragma unroll
+                for (int m = 0; m < TM; ++m) a[m] = A[m * C::DT * W + j];
+#pragma unroll
+                for (int m = 0; m < TM; ++m)
+#pragma unroll
+                    for (int n = 0; n < TN; ++n) y[m][n] = fma(a[m], b[n], y[m][n]);
+            }
+            T f[TN];
+            lds_vec<T, TN>(Fa + i * TRT + tr * TN, f);
+#pragma unroll
+            for (int n = 0; n < TN; ++n)
+#pragma unroll
+                for (int m = 0; m < TM; ++m) acc[m][n] = fma(f[n], y[m][n], acc[m][n]);
+        }
+        // buffer buf and (at a channel change) Fa/Fb are rewritten next
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && dead) {
+        // let the copies already issued land before the CTA exits
+        for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k) {
+            const unsigned long long t0 = cc_gtimer();
+            while (!cc_mbar_try(bar0 + 8u * (k & 1), (uint32_t)(k >> 1) & 1u) && cc_gtimer() - t0 < FAC_WAIT_NS) {
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int n = 0; n < TN; ++n) {
+            const int d = d0 + td + m * C::DT, r = r0 + tr * TN + n;
+            if (d < tv.ndata && r < R) part[((size_t)sp * R + r) * tv.ndata + d] = acc[m][n];
+        }
+}
+
+// ----------------------------------------------------------------------------
 // Adjoint.  W[e][r] = sum_d FK[d][e] gO[r][d] over a tile of 128 elements x 64
 // replicas, K = data points.
 // ----------------------------------------------------------------------------
@@ -530,13 +755,45 @@ int num_sms() {
     return n;
 }
 
+// Channel splits of the factorised kernel: a function of the table only, so a
+// replica's summation order does not depend on R (bit-exact batching).
+int fac_nsplit(const fk_table *t) {
+    const int dt = (t->ndata + FAC_TDT - 1) / FAC_TDT;
+    const long long want = (2LL * num_sms() + dt - 1) / dt;
+    return (int)std::max(1LL, std::min((long long)t->nch, want));
+}
+
+template <typename T, int TRT>
+int launch_fac_t(const fk_table *t, const T *F, int R, const T *fk, int nsplit, T *part, cudaStream_t s) {
+    const size_t smem = fac_smem<T, TRT>(t->nx);
+    // opt in once at the largest x grid so that every table fits
+    int rc = set_smem<T>(k_fac<T, TRT>, fac_smem<T, TRT>(MAX_NX));
+    if (rc) return rc;
+    CUtensorMap map;
+    rc = make_plain_map(&map, fk, (int)sizeof(T), t->ldE, t->ndata, fac_width(t->nx, sizeof(T)), FAC_TDT);
+    if (rc) return rc;
+    dim3 grid((t->ndata + FAC_TDT - 1) / FAC_TDT, (R + TRT - 1) / TRT, nsplit);
+    k_fac<T, TRT><<<grid, 256, smem, s>>>(map, view(t), F, R, nsplit, part);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+// Hadronic, R >= 2: replica tiles of 16 for few replicas, else the widest
+// tile the registers allow (64 in FP32, 32 in FP64).
+template <typename T>
+int launch_fac(const fk_table *t, const T *F, int R, const T *fk, int nsplit, T *part, cudaStream_t s) {
+    if (R <= 16) return launch_fac_t<T, 16>(t, F, R, fk, nsplit, part, s);
+    return launch_fac_t<T, sizeof(T) == 4 ? 64 : 32>(t, F, R, fk, nsplit, part, s);
+}
+
 template <int KIND, typename T>
 int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, cudaStream_t s) {
     TableView tv = view(t);
     Scratch scr(s);
     T *part = nullptr;
     int nparts;
-    if (R <= 4) {
+    if (R <= 4 && (KIND == FK_KIND_DIS || R == 1)) {
         constexpr int CH = 256 * V16<T>::n * StreamCfg<T>::U;
         const int nchunk = (int)((t->ldE + CH - 1) / CH);
         nparts = nchunk;
@@ -545,6 +802,11 @@ int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, c
         k_stream<KIND, T><<<grid, 256, 0, s>>>(tv, fk, F, R, part);
         count_launch();
         FK_CUDA(cudaGetLastError());
+    } else if (KIND == FK_KIND_HAD) {
+        nparts = fac_nsplit(t);
+        FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
+        int rc = launch_fac<T>(t, F, R, fk, nparts, part, s);
+        if (rc) return rc;
     } else {
         const int dt = (t->ndata + TDT - 1) / TDT, rt = (R + TRT - 1) / TRT;
         const long long nseg = KIND == FK_KIND_HAD ? t->nch : (t->E + TileCfg<T>::KC - 1) / TileCfg<T>::KC;
@@ -701,13 +963,11 @@ template <typename T>
 int had_noalloc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, cudaStream_t s) {
     TableView tv = view(t);
     int nparts;
-    if (R <= 4) {
+    if (R == 1) {
         constexpr int CH = 256 * V16<T>::n * StreamCfg<T>::U;
         nparts = (int)((t->ldE + CH - 1) / CH);
     } else {
-        const int dt = (t->ndata + TDT - 1) / TDT;
-        const long long want = (2LL * num_sms() + dt - 1) / dt;
-        nparts = (int)std::max(1LL, std::min((long long)t->nch, want));
+        nparts = fac_nsplit(t);
     }
     const size_t need = sizeof(T) * (size_t)nparts * R * t->ndata;
     if (need > FK_NOALLOC_BYTES)
@@ -718,19 +978,14 @@ int had_noalloc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     T *part = static_cast<T *>(scratch);
-    if (R <= 4) {
+    if (R == 1) {
         dim3 grid(nparts, (t->ndata + StreamCfg<T>::DB - 1) / StreamCfg<T>::DB, R);
         k_stream<FK_KIND_HAD, T><<<grid, 256, 0, s>>>(tv, fk, F, R, part);
         count_launch();
         FK_CUDA(cudaGetLastError());
     } else {
-        constexpr size_t smem = tile_smem<T>();
-        rc = set_smem<T>(k_tile<FK_KIND_HAD, T>, smem);
+        rc = launch_fac<T>(t, F, R, fk, nparts, part, s);
         if (rc) return rc;
-        dim3 grid((t->ndata + TDT - 1) / TDT, (R + TRT - 1) / TRT, nparts);
-        k_tile<FK_KIND_HAD, T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
-        count_launch();
-        FK_CUDA(cudaGetLastError());
     }
     const long long n = (long long)R * t->ndata;
     k_reduce_parts<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nparts, t->ndata, R, O, ldo);
@@ -804,3 +1059,15 @@ extern "C" int fk_grad_sum(const void *const *parts, int nparts, long long n, vo
     return prec == FK_FP64 ? grad_sum_t<double>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream)
                            : grad_sum_t<float>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream);
 }
+
+namespace fk {
+int cc_device_status(int reset) {
+    int v = 0;
+    FK_CUDA(cudaMemcpyFromSymbol(&v, g_fk_cc_error, sizeof(int)));
+    if (reset) {
+        const int z = 0;
+        FK_CUDA(cudaMemcpyToSymbol(g_fk_cc_error, &z, sizeof(int)));
+    }
+    return v ? FK_ETIMEDOUT : FK_OK;
+}
+}  // namespace fk

@@ -1280,6 +1280,22 @@ void tc_free(fk_table *t) {
     t->tc.gmap = nullptr;
 }
 
+int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_cols,
+                   int box_rows) {
+    auto fn = encoder();
+    if (!fn) return fail(FK_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return FK_OK;
+}
+
 int device_status(int reset) {
     int v = 0;
     FK_CUDA(cudaMemcpyFromSymbol(&v, g_fk_device_error, sizeof(int)));

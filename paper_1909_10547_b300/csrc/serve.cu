@@ -227,7 +227,15 @@ void launch_batch(fk_server *s, Batch *b) {
     }
 }
 
-int kernel_class(int prec, int R) { return (prec == FK_FP64 || prec == FK_FP32) ? (R <= 4 ? 0 : 1) : 2; }
+// Requests are merged only within one kernel class, so that a replica's
+// result is the same alone and in any batch: the FP64/FP32 hadronic path
+// streams R = 1 and uses the factorised kernel for R >= 2 (DIS: R <= 4 and
+// R > 4); each tensor-core precision is a single class.
+int kernel_class(const fk_table *t, int prec, int R) {
+    if (prec != FK_FP64 && prec != FK_FP32) return 2;
+    if (t->kind == FK_KIND_HAD) return R == 1 ? 0 : 1;
+    return R <= 4 ? 0 : 1;
+}
 
 void scheduler(fk_server *s) {
     cudaSetDevice(s->device);
@@ -262,13 +270,13 @@ void scheduler(fk_server *s) {
         }
         Batch *b = new Batch();
         b->srv = s;
-        const int cls = kernel_class(head->prec, head->R);
+        const int cls = kernel_class(t, head->prec, head->R);
         int R = 0;
         for (auto it = s->queue.begin(); it != s->queue.end();) {
             Request *r = *it;
             const int Rn = R + r->R;
             const bool same = r->table == head->table && r->prec == head->prec &&
-                              kernel_class(r->prec, r->R) == cls && kernel_class(r->prec, Rn) == cls;
+                              kernel_class(t, r->prec, r->R) == cls && kernel_class(t, r->prec, Rn) == cls;
             const size_t add = request_device_bytes(t, Rn, r->prec) - (R ? request_device_bytes(t, R, r->prec) : 0);
             if (same && (b->reqs.empty() || s->resident + s->inflight_bytes + b->bytes + add <= s->budget)) {
                 b->reqs.push_back(r);

@@ -90,7 +90,7 @@ struct TcPack {
 };
 
 struct TcLayout {
-    int G = 0;          // data points per tile (power of two, G * nx <= 256)
+    int G = 0;          // data points per tile (4, 5, 6, 7, 8, 12 or 16; G * nx <= 256)
     int ntile_n = 0;    // ceil(ndata / G)
     int n_rows = 0;     // MMA N = G * nx rounded up to 16
     TcPack fwd, bwd;

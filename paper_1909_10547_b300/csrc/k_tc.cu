@@ -615,8 +615,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     acc[dl] = (r < p.R && dd < p.ndata) ? __ldg(p.gO + (size_t)r * p.ldo + dd) : 0.f;
                 }
             }
-            const int ncols = G * p.nx;  // accumulator columns in use
-            constexpr int MI = 256 / G;  // x points a 256-column accumulator can hold
+            const int ncols = G * p.nx;      // accumulator columns in use: column i * G + dl
+            constexpr int MI = 255 / G + 1;  // x points a 256-column accumulator can hold
             for (int g = 0; g < p.ngroups; ++g, ++gc) {
                 const int b = gc & 1;
                 // the multipliers f^r_{a_g}(x_i) do not depend on the MMA:
@@ -637,31 +637,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-                float *pg = MODE == MODE_ADJ ? p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r : nullptr;
-                // 64 columns per TMEM round trip; columns of x points >= nx
-                // (never written by the MMA) are skipped, not multiplied by 0
+                // adjoint: per x point, the sum over the tile's data points
+                float ps[MODE == MODE_ADJ ? MI : 1];
+                if (MODE == MODE_ADJ) {
+#pragma unroll
+                    for (int i = 0; i < MI; ++i) ps[i] = 0.f;
+                }
+                // 64 columns per TMEM round trip; the column -> (x point,
+                // data point) split is fixed at compile time; columns of x
+                // points >= nx (never written by the MMA) are skipped
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c * 64 < ncols) {
                         uint32_t v[64];
                         tmem_ld64(taddr + (uint32_t)(c * 64), v);
 #pragma unroll
-                        for (int u = 0; u < 64 / G; ++u) {
-                            const int i = c * (64 / G) + u;
+                        for (int k = 0; k < 64; ++k) {
+                            const int col = c * 64 + k, i = col / G, dl = col % G;
                             if (i < p.nx) {
-                                if (MODE == MODE_FWD) {
-#pragma unroll
-                                    for (int dl = 0; dl < G; ++dl)
-                                        acc[dl] = fmaf(m[i], __uint_as_float(v[u * G + dl]), acc[dl]);
-                                } else {
-                                    float s = 0.f;
-#pragma unroll
-                                    for (int dl = 0; dl < G; ++dl) s = fmaf(acc[dl], __uint_as_float(v[u * G + dl]), s);
-                                    pg[(size_t)i * p.R_pad] = s;
-                                }
+                                if (MODE == MODE_FWD)
+                                    acc[dl] = fmaf(m[i], __uint_as_float(v[k]), acc[dl]);
+                                else
+                                    ps[i] = fmaf(acc[dl], __uint_as_float(v[k]), ps[i]);
                             }
                         }
                     }
+                }
+                if (MODE == MODE_ADJ) {
+                    float *pg = p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r;
+#pragma unroll
+                    for (int i = 0; i < MI; ++i)
+                        if (i < p.nx) pg[(size_t)i * p.R_pad] = ps[i];
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -1010,7 +1016,11 @@ int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2
     const BMaps mb = b_maps<PREC>(pk);
     switch (t->tc.G) {
         case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mb, p, s);
+        case 5: return launch_tc<PREC, 5, MODE>(t, mA, mA2, mb, p, s);
+        case 6: return launch_tc<PREC, 6, MODE>(t, mA, mA2, mb, p, s);
+        case 7: return launch_tc<PREC, 7, MODE>(t, mA, mA2, mb, p, s);
         case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mb, p, s);
+        case 12: return launch_tc<PREC, 12, MODE>(t, mA, mA2, mb, p, s);
         case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mb, p, s);
     }
     return fail(FK_EINVAL, "bad tile height");
@@ -1163,7 +1173,15 @@ int tc_build(fk_table *t, const double *host_fk) {
     TcLayout &L = t->tc;
     make_groups(t, t->ca, L.fwd);
     make_groups(t, t->cb, L.bwd);
-    L.G = t->nx <= 16 ? 16 : (t->nx <= 32 ? 8 : 4);
+    // data points per tile: the largest G of the compiled set with G * nx <=
+    // 256 (MMA N and one TMEM accumulator): wider MMAs do more work per
+    // instruction issued
+    L.G = 4;
+    for (int g : {16, 12, 8, 7, 6, 5, 4})
+        if (g * t->nx <= 256) {
+            L.G = g;
+            break;
+        }
     L.n_rows = (L.G * t->nx + 15) / 16 * 16;
     L.ntile_n = (t->ndata + L.G - 1) / L.G;
     const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));

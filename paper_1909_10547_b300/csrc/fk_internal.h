@@ -71,7 +71,7 @@ struct TcGroups {
 struct TcPack {
     TcGroups grp{};
     int ktot = 0;       // used K (sum of padded group lengths)
-    int ktot_pad = 0;   // row length, a multiple of 64
+    int ktot_pad = 0;   // row length: whole pipeline stages (a multiple of 64 or 128)
     __nv_bfloat16 *hi = nullptr;  // BF16 / hi part
     __nv_bfloat16 *lo = nullptr;  // lo part (BF16X3)
     float *f32 = nullptr;         // TF32 operand (FP32 bits, rounded)

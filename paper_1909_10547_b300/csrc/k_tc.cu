@@ -277,13 +277,17 @@ struct Tr {
     static constexpr int KC = 128 / ESZ;      // K elements per 128-byte swizzled row
     static constexpr int KSTEP = 32 / ESZ;    // K per MMA instruction
     static constexpr int NOPS = X3 ? 2 : 1;   // operand copies (hi, lo)
+    // 128-byte swizzle atoms per stage along K: two for the single-copy modes
+    // (8 MMAs between stage barriers), one for hi+lo (already 12 MMAs)
+    static constexpr int ATOMS = X3 ? 1 : 2;
+    static constexpr int KCS = KC * ATOMS;    // K elements per stage
     static constexpr uint32_t FMT = PREC == FK_TF32 ? 2u : 1u;  // TF32 : BF16
 };
 // Pipeline depth: a CTA of a pair holds half of each B tile, so its stages
 // are smaller and more of them fit.
 template <int PREC, int CL>
 __host__ __device__ constexpr int tc_stages() {
-    return CL == 2 ? (Tr<PREC>::X3 ? 3 : 6) : (Tr<PREC>::X3 ? 2 : 4);
+    return CL == 2 ? 3 : 2;
 }
 
 struct TcParams {
@@ -303,7 +307,7 @@ enum { MODE_FWD = 0, MODE_ADJ = 1 };
 
 template <int PREC, int CL>
 size_t tc_smem_bytes(int n_rows) {
-    const size_t stage = (size_t)Tr<PREC>::NOPS * (TC_M * 128 + (size_t)(n_rows / CL) * 128);
+    const size_t stage = (size_t)Tr<PREC>::NOPS * Tr<PREC>::ATOMS * (TC_M * 128 + (size_t)(n_rows / CL) * 128);
     return 1024 + tc_stages<PREC, CL>() * stage + 256;
 }
 
@@ -344,7 +348,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     const int b_rows = p.n_rows / CL;  // B rows held by this CTA
     const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)b_rows * 128;
-    const uint32_t stage_bytes = T::NOPS * (a_bytes + b_bytes);
+    const uint32_t stage_bytes = T::NOPS * T::ATOMS * (a_bytes + b_bytes);
+    // a stage: the A atoms, then the B atoms (then the lo copies for hi+lo)
+    const uint32_t offB = T::ATOMS * a_bytes, offA2 = T::ATOMS * (a_bytes + b_bytes), offB2 = offA2 + offB;
     const uint32_t bar0 = base + S * stage_bytes;
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (S + s); };
@@ -402,8 +408,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             u2 += p.ngroups;
             ++back;
         }
-        const int e2 = (p.kend[u2] + T::KC - 1) / T::KC - back * p.nchunks;  // stage after its last
-        if (p.kbeg[g] / T::KC - S - e2 >= PW_SLACK) pwait |= 1u << g;
+        const int e2 = (p.kend[u2] + T::KCS - 1) / T::KCS - back * p.nchunks;  // stage after its last
+        if (p.kbeg[g] / T::KCS - S - e2 >= PW_SLACK) pwait |= 1u << g;
     }
 
     if (warp == 0 && lane == 0) {
@@ -420,7 +426,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (leader) {
                     // the accumulator of every group starting in this stage
                     // must be free before the MMAs can read the stage
-                    while (pg < p.ngroups && p.kbeg[pg] < (q + 1) * T::KC) {
+                    while (pg < p.ngroups && p.kbeg[pg] < (q + 1) * T::KCS) {
                         if (((pwait >> pg) & 1u) && !mbar_wait(acce(pgc & 1), ((pgc >> 1) & 1) ^ 1, dead)) {
                             ok = false;
                             break;
@@ -438,19 +444,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (CL == 2) {
                     const uint32_t fb = mapa(full(s), 0);
                     if (leader) mbar_expect_tx(full(s), 2 * stage_bytes);
-                    tma_load_2d_pair(st, &mapA, fb, q * T::KC, rt * TC_M);
-                    tma_load_2d_pair(st + a_bytes, &mapB, fb, q * T::KC, brow);
-                    if (T::X3) {
-                        tma_load_2d_pair(st + a_bytes + b_bytes, &mapA2, fb, q * T::KC, rt * TC_M);
-                        tma_load_2d_pair(st + 2 * a_bytes + b_bytes, &mapB2, fb, q * T::KC, brow);
+#pragma unroll
+                    for (int a = 0; a < T::ATOMS; ++a) {
+                        const int x = q * T::KCS + a * T::KC;
+                        tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, rt * TC_M);
+                        tma_load_2d_pair(st + offB + a * b_bytes, &mapB, fb, x, brow);
+                        if (T::X3) {
+                            tma_load_2d_pair(st + offA2 + a * a_bytes, &mapA2, fb, x, rt * TC_M);
+                            tma_load_2d_pair(st + offB2 + a * b_bytes, &mapB2, fb, x, brow);
+                        }
                     }
                 } else {
                     mbar_expect_tx(full(s), stage_bytes);
-                    tma_load_2d(st, &mapA, full(s), q * T::KC, rt * TC_M);
-                    tma_load_2d(st + a_bytes, &mapB, full(s), q * T::KC, brow);
-                    if (T::X3) {
-                        tma_load_2d(st + a_bytes + b_bytes, &mapA2, full(s), q * T::KC, rt * TC_M);
-                        tma_load_2d(st + 2 * a_bytes + b_bytes, &mapB2, full(s), q * T::KC, brow);
+#pragma unroll
+                    for (int a = 0; a < T::ATOMS; ++a) {
+                        const int x = q * T::KCS + a * T::KC;
+                        tma_load_2d(st + a * a_bytes, &mapA, full(s), x, rt * TC_M);
+                        tma_load_2d(st + offB + a * b_bytes, &mapB, full(s), x, brow);
+                        if (T::X3) {
+                            tma_load_2d(st + offA2 + a * a_bytes, &mapA2, full(s), x, rt * TC_M);
+                            tma_load_2d(st + offB2 + a * b_bytes, &mapB2, full(s), x, brow);
+                        }
                     }
                 }
             }
@@ -508,20 +522,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t st = base + s * stage_bytes;
-                if (kw >= (q + 1) * T::KC) {
+                if (kw >= (q + 1) * T::KCS) {
 #pragma unroll
-                    for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
-                        const int k = q * T::KC + ks * T::KSTEP;
+                    for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
+                        const int k = q * T::KCS + ks * T::KSTEP;
                         if (g >= p.ngroups) break;  // K padding after the last group
                         const int b = gc & 1;
                         const uint32_t d = tmem + (uint32_t)(b * 256);
-                        const uint32_t off = (uint32_t)ks * 32u;
-                        const uint64_t ah = sw128_desc(st + off);
-                        const uint64_t bh = sw128_desc(st + a_bytes + off);
+                        // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
+                        const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
+                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
+                        const uint64_t ah = sw128_desc(st + atom * a_bytes + off);
+                        const uint64_t bh = sw128_desc(st + offB + atom * b_bytes + off);
                         mma<PREC, CL>(d, ah, bh, idesc, k != kb);
                         if (T::X3) {
-                            const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
-                            const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
+                            const uint64_t al = sw128_desc(st + offA2 + atom * a_bytes + off);
+                            const uint64_t bl = sw128_desc(st + offB2 + atom * b_bytes + off);
                             mma<PREC, CL>(d, ah, bl, idesc, 1);
                             mma<PREC, CL>(d, al, bh, idesc, 1);
                         }
@@ -539,8 +555,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                     }
                 } else {
-                    for (int ks = 0; ks < T::KC / T::KSTEP; ++ks) {
-                        const int k = q * T::KC + ks * T::KSTEP;
+                    for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
+                        const int k = q * T::KCS + ks * T::KSTEP;
                         if (g >= p.ngroups) break;
                         const int b = gc & 1;
                         if (k == kb && ((mwait >> g) & 1u)) {
@@ -551,13 +567,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             tc_fence_after();
                         }
                         const uint32_t d = tmem + (uint32_t)(b * 256);
-                        const uint32_t off = (uint32_t)ks * 32u;
-                        const uint64_t ah = sw128_desc(st + off);
-                        const uint64_t bh = sw128_desc(st + a_bytes + off);
+                        // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
+                        const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
+                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
+                        const uint64_t ah = sw128_desc(st + atom * a_bytes + off);
+                        const uint64_t bh = sw128_desc(st + offB + atom * b_bytes + off);
                         mma<PREC, CL>(d, ah, bh, idesc, k != kb);
                         if (T::X3) {
-                            const uint64_t al = sw128_desc(st + a_bytes + b_bytes + off);
-                            const uint64_t bl = sw128_desc(st + 2 * a_bytes + b_bytes + off);
+                            const uint64_t al = sw128_desc(st + offA2 + atom * a_bytes + off);
+                            const uint64_t bl = sw128_desc(st + offB2 + atom * b_bytes + off);
                             mma<PREC, CL>(d, ah, bl, idesc, 1);
                             mma<PREC, CL>(d, al, bh, idesc, 1);
                         }
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     // the next wait is at a group that has not started yet:
                     // group g itself if it begins at the next stage
-                    kw = next_wait_k(g < p.ngroups && kb >= (q + 1) * T::KC ? g : g + 1);
+                    kw = next_wait_k(g < p.ngroups && kb >= (q + 1) * T::KCS ? g : g + 1);
                 }
                 if (CL == 2)
                     mma_commit_pair(empty(s));
@@ -1061,7 +1079,7 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     p = TcParams{};
     p.nrt = R_pad / TC_M;
     p.ntiles = L.ntile_n * p.nrt;
-    p.nchunks = pk.ktot_pad / Tr<PREC>::KC;
+    p.nchunks = pk.ktot_pad / Tr<PREC>::KCS;
     p.n_rows = L.n_rows;
     p.ngroups = pk.grp.ngroups;
     p.nx = t->nx;
@@ -1164,7 +1182,10 @@ void make_groups(const fk_table *t, const std::vector<int> &key, TcPack &pk) {
         }
     }
     pk.ktot = k;
-    pk.ktot_pad = (k + 63) / 64 * 64;
+    // whole pipeline stages: 128 K elements for BF16 and TF32 (two swizzle
+    // atoms per stage), 64 when the table holds only the hi+lo operands
+    const int kal = (t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_TF32))) ? 128 : 64;
+    pk.ktot_pad = (k + kal - 1) / kal * kal;
 }
 
 }  // namespace

@@ -283,7 +283,7 @@ def traffic_of(kernel, prec, ndata, replicas):
     """DRAM bytes per launch of `kernel` for this stress workload, from the
     committed ncu capture list (profiles/dram_traffic.txt), or None when no
     capture matches or the kernel's source has changed since it was taken."""
-    src = {"k_tc": "k_tc.cu", "k_stream": "k_cc.cu"}[kernel]
+    src = {"k_tc": "k_tc.cu", "k_stream": "k_cc.cu", "k_fac": "k_cc.cu"}[kernel]
     here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "paper_1909_10547_b300", "csrc", src), "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
@@ -354,7 +354,7 @@ def run_stress(args):
         roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": ach / tpeak, "traffic": None}
     roof["peak_source"] = src
-    kern = "k_tc" if tc else ("k_stream" if R <= 4 and args.prec in ("fp32", "fp64") else None)
+    kern = "k_tc" if tc else ("k_stream" if R == 1 else "k_fac")
     if kern:
         roof["kernel"] = f"{kern} (timed as the whole convolution call, operand packing included)"
         roof["traffic"] = traffic_of(kern, args.prec, args.ndata, R) if args.table == "stress" else None

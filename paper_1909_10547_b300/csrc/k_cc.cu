@@ -340,10 +340,16 @@ __host__ __device__ constexpr int fac_width(int nx, int esz) {
     return w;
 }
 
+// rows of the staged second-flavour PDF column: x points -FAC_PAD .. nx + 2 FAC_PAD
+// (zero outside [0, nx)), so that a box column j' reads the PDF of x point
+// j' - rem (rem < 16 bytes' worth of elements) without bounds tests
+constexpr int FAC_PAD = 4;
+
 template <typename T, int TRT>
 size_t fac_smem(int nx) {
-    // 1024 for alignment of the TMA destination, two boxes, two PDF columns
-    return 1024 + sizeof(T) * (2 * (size_t)FAC_TDT * fac_width(nx, sizeof(T)) + 2 * (size_t)nx * TRT);
+    // 1024 for alignment of the TMA destination, two boxes, the two PDF columns
+    return 1024 + sizeof(T) * (2 * (size_t)FAC_TDT * fac_width(nx, sizeof(T)) + (size_t)nx * TRT +
+                               (size_t)(nx + 3 * FAC_PAD) * TRT);
 }
 
 // N consecutive values from shared memory in 16-byte loads
@@ -389,7 +395,7 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
     const uint32_t abase = (raw + 1023u) & ~1023u;
     T *As = reinterpret_cast<T *>(smem_raw + (abase - raw));  // [2][FAC_TDT][W]
     T *Fa = As + 2 * FAC_TDT * W;                                // [nx][TRT]
-    T *Fb = Fa + nx * TRT;                                       // [nx][TRT]
+    T *Fb = Fa + nx * TRT;                                       // [nx + 3 FAC_PAD][TRT], row j + FAC_PAD
     const uint32_t box_bytes = (uint32_t)(FAC_TDT * W * sizeof(T));
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
 
@@ -448,15 +454,12 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
             for (int idx = threadIdx.x; idx < nx * TRT; idx += 256) {
                 const int k = idx / TRT, rr = idx - k * TRT;
                 const int r = r0 + rr;
-                T va = T(0), vb = T(0);
-                if (r < R) {
-                    const T *Fr = F + (size_t)r * fstride;
-                    const int m = tv.xmap[k];
-                    va = Fr[fa * tv.nxg + m];
-                    vb = Fr[fb * tv.nxg + m];
-                }
-                Fa[idx] = va;
-                Fb[idx] = vb;
+                Fa[idx] = r < R ? F[(size_t)r * fstride + fa * tv.nxg + tv.xmap[k]] : T(0);
+            }
+            for (int idx = threadIdx.x; idx < (nx + 3 * FAC_PAD) * TRT; idx += 256) {
+                const int k = idx / TRT - FAC_PAD, rr = idx % TRT;
+                const int r = r0 + rr;
+                Fb[idx] = (r < R && k >= 0 && k < nx) ? F[(size_t)r * fstride + fb * tv.nxg + tv.xmap[k]] : T(0);
             }
             cur_c = c;
         }
@@ -479,24 +482,30 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
             }
         }
         if (!dead) {
+            // box column j' holds x point j' - rem; columns outside [rem, rem + nx)
+            // meet zero PDF rows.  JV columns per 16-byte load of a row.
+            constexpr int JV = 16 / (int)sizeof(T);
             const int rem = (int)(step_off(s_) % E16);
-            const T *A = As + buf * FAC_TDT * W + td * W + rem;
-            const T *B = Fb + tr * TN;
+            const int ncol = (rem + nx + JV - 1) / JV * JV;
+            const T *A = As + buf * FAC_TDT * W + td * W;
+            const T *B = Fb + (FAC_PAD - rem) * TRT + tr * TN;
             T y[TM][TN];
 #pragma unroll
             for (int m = 0; m < TM; ++m)
 #pragma unroll
                 for (int n = 0; n < TN; ++n) y[m][n] = T(0);
-#pragma unroll 2
-            for (int j = 0; j < nx; ++j) {
-                T a[TM], b[TN];
-                lds_vec<T, TN>(B + j * TRT, b);
+            for (int j = 0; j < ncol; j += JV) {
+                T a[TM][JV], b[JV][TN];
 #pragma unroll
-                for (int m = 0; m < TM; ++m) a[m] = A[m * C::DT * W + j];
+                for (int m = 0; m < TM; ++m) lds_vec<T, JV>(A + m * C::DT * W + j, a[m]);
 #pragma unroll
-                for (int m = 0; m < TM; ++m)
+                for (int jj = 0; jj < JV; ++jj) lds_vec<T, TN>(B + (j + jj) * TRT, b[jj]);
 #pragma unroll
-                    for (int n = 0; n < TN; ++n) y[m][n] = fma(a[m], b[n], y[m][n]);
+                for (int jj = 0; jj < JV; ++jj)
+#pragma unroll
+                    for (int m = 0; m < TM; ++m)
+#pragma unroll
+                        for (int n = 0; n < TN; ++n) y[m][n] = fma(a[m][jj], b[jj][n], y[m][n]);
             }
             T f[TN];
             lds_vec<T, TN>(Fa + i * TRT + tr * TN, f);

@@ -311,9 +311,10 @@ __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict_
 // A CTA owns FAC_TDT data points x TRT replicas and the channels of its split.
 // Y is a register-blocked product (each thread TM data points x TN replicas,
 // K = the nx points x_j).  The FK rows of step (c, i) arrive by one TMA copy
-// of a FAC_TDT x W box (W >= nx + the 16-byte alignment remainder), double
-// buffered on two mbarriers so that the next step's copy overlaps this step's
-// products; the two PDF columns of the channel are staged once per channel.
+// of a FAC_TDT x W box (W >= nx + the 16-byte alignment remainder), NBUF
+// boxes in flight on their mbarriers so that later steps' copies overlap this
+// step's products; the two PDF columns of the channel are staged once per
+// channel.
 // The table is read once per replica tile.
 // grid (ceil(ndata / FAC_TDT), ceil(R / TRT), nsplit);
 // part[(split * R + r) * ndata + d] as for k_tile.
@@ -326,6 +327,9 @@ struct FacCfg {
     static constexpr int RT = TRT / TN;                 // threads along replicas
     static constexpr int DT = 256 / RT;                 // threads along data points
     static constexpr int TM = FAC_TDT / DT;             // data points per thread: td + m * DT
+    // table boxes in flight (three measured slower than two for R <= 16:
+    // fewer CTAs fit per SM)
+    static constexpr int NBUF = 2;
     static_assert(RT * DT == 256 && TM * DT == FAC_TDT, "tile shape");
 };
 
@@ -347,8 +351,8 @@ constexpr int FAC_PAD = 4;
 
 template <typename T, int TRT>
 size_t fac_smem(int nx) {
-    // 1024 for alignment of the TMA destination, two boxes, the two PDF columns
-    return 1024 + sizeof(T) * (2 * (size_t)FAC_TDT * fac_width(nx, sizeof(T)) + (size_t)nx * TRT +
+    // 1024 for alignment of the TMA destination, the boxes, the two PDF columns
+    return 1024 + sizeof(T) * (FacCfg<T, TRT>::NBUF * (size_t)FAC_TDT * fac_width(nx, sizeof(T)) + (size_t)nx * TRT +
                                (size_t)(nx + 3 * FAC_PAD) * TRT);
 }
 
@@ -389,12 +393,13 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
     using C = FacCfg<T, TRT>;
     constexpr int TM = C::TM, TN = C::TN, E16 = 16 / (int)sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2];
+    constexpr int NB = C::NBUF;
+    __shared__ __align__(8) uint64_t bars[NB];
     const int nx = tv.nx, W = fac_width(nx, sizeof(T));
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t abase = (raw + 1023u) & ~1023u;
-    T *As = reinterpret_cast<T *>(smem_raw + (abase - raw));  // [2][FAC_TDT][W]
-    T *Fa = As + 2 * FAC_TDT * W;                                // [nx][TRT]
+    T *As = reinterpret_cast<T *>(smem_raw + (abase - raw));  // [NB][FAC_TDT][W]
+    T *Fa = As + NB * FAC_TDT * W;                               // [nx][TRT]
     T *Fb = Fa + nx * TRT;                                       // [nx + 3 FAC_PAD][TRT], row j + FAC_PAD
     const uint32_t box_bytes = (uint32_t)(FAC_TDT * W * sizeof(T));
     const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
@@ -407,8 +412,8 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
     const size_t fstride = (size_t)NFL * tv.nxg;
 
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        for (int b = 0; b < NB; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map) : "memory");
     }
@@ -439,13 +444,12 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
 
     bool dead = false;
     int issued = 0;  // copies issued by thread 0
-    if (threadIdx.x == 0 && nsteps > 0) {
-        stage(0, 0);
-        issued = 1;
-    }
+    if (threadIdx.x == 0)
+        for (; issued < NB - 1 && issued < nsteps; ++issued) stage(issued, issued);
     int cur_c = -1;
     for (int s_ = 0; s_ < nsteps; ++s_) {
-        const int buf = s_ & 1;
+        const int buf = s_ % NB;
+        const uint32_t par = (uint32_t)(s_ / NB) & 1u;  // phase s / NB of its buffer's barrier
         const int c = c_b + s_ / nx, i = s_ - (s_ / nx) * nx;
         if (c != cur_c) {
             // new channel: its two PDF columns (every thread is past the
@@ -463,17 +467,17 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
             }
             cur_c = c;
         }
-        // the next step's box streams in while this step computes (its
-        // buffer was released by the barrier that ended the previous step)
-        if (threadIdx.x == 0 && s_ + 1 < nsteps && !dead) {
-            stage(s_ + 1, buf ^ 1);
+        // step s + NB - 1 streams in while this one computes (its buffer,
+        // that of step s - 1, was released by the barrier ending step s - 1)
+        if (threadIdx.x == 0 && s_ + NB - 1 < nsteps && !dead) {
+            stage(s_ + NB - 1, (s_ + NB - 1) % NB);
             ++issued;
         }
         __syncthreads();  // Fa/Fb written
         // wait for this step's box (phase s/2 of its buffer's barrier)
-        if (!dead && !cc_mbar_try(bar0 + 8u * buf, (uint32_t)(s_ >> 1) & 1u)) {
+        if (!dead && !cc_mbar_try(bar0 + 8u * buf, par)) {
             const unsigned long long t0 = cc_gtimer();
-            while (!cc_mbar_try(bar0 + 8u * buf, (uint32_t)(s_ >> 1) & 1u)) {
+            while (!cc_mbar_try(bar0 + 8u * buf, par)) {
                 if (cc_gtimer() - t0 > FAC_WAIT_NS) {
                     dead = true;
                     atomicExch(&g_fk_cc_error, 1);
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
             constexpr int JV = 16 / (int)sizeof(T);
             const int rem = (int)(step_off(s_) % E16);
             const int ncol = (rem + nx + JV - 1) / JV * JV;
-            const T *A = As + buf * FAC_TDT * W + td * W;
+            const T *A = As + buf * FAC_TDT * W + td * W;  // this step's box
             const T *B = Fb + (FAC_PAD - rem) * TRT + tr * TN;
             T y[TM][TN];
 #pragma unroll
@@ -519,9 +523,9 @@ __global__ void __launch_bounds__(256) k_fac(const __grid_constant__ CUtensorMap
     }
     if (threadIdx.x == 0 && dead) {
         // let the copies already issued land before the CTA exits
-        for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k) {
+        for (int k = (issued > NB ? issued - NB : 0); k < issued; ++k) {
             const unsigned long long t0 = cc_gtimer();
-            while (!cc_mbar_try(bar0 + 8u * (k & 1), (uint32_t)(k >> 1) & 1u) && cc_gtimer() - t0 < FAC_WAIT_NS) {
+            while (!cc_mbar_try(bar0 + 8u * (k % NB), (uint32_t)(k / NB) & 1u) && cc_gtimer() - t0 < FAC_WAIT_NS) {
             }
         }
     }

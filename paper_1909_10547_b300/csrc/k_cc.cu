@@ -1,13 +1,16 @@
 // CUDA-core kernels of the FK convolution in FP64 and FP32.
 //
-//  * k_stream : few replicas (R <= 4).  The observable is a dot product of the
+//  * k_stream : one replica (hadronic) or R <= 4 (DIS).  The observable is a dot product of the
 //    table row FK[d][.] with the weight vector w[e] (hadronic, Eq. 1:
 //    w[(c,i,j)] = f_{a_c}(x_i) f_{b_c}(x_j); DIS: w[(k,i)] = f_{a_k}(x_i)).
 //    The table is streamed once with 16-byte loads; each CTA owns an element
 //    chunk, keeps its weights in registers and reuses them over DB data points.
-//  * k_tile   : many replicas.  O[d][r] = sum_e FK[d][e] w[e][r] as a tiled
-//    product whose second operand is formed on the fly in shared memory from
-//    the two PDFs of the current channel (never materialised in HBM).
+//  * k_fac    : hadronic, R >= 2.  Eq. 1 factorised per channel and x_i of
+//    its first flavour: a register-blocked product over x_j with the second
+//    flavour's PDF, folded into O with the first flavour's PDF; table rows
+//    staged by TMA.
+//  * k_tile   : DIS, R > 4.  O[d][r] = sum_k FK[d][k] F[r][k] as a tiled
+//    product (K = active flavour x point).
 //  * k_bwd_*  : the adjoint.  W[e][r] = sum_d FK[d][e] gO[r][d] is formed per
 //    tile, then contracted with the PDF of the other flavour of the channel
 //    (product rule on each term of Eq. 1).
@@ -164,7 +167,9 @@ __global__ void k_reduce_parts(const T *__restrict__ part, int nparts, int ndata
 }
 
 // ----------------------------------------------------------------------------
-// Many-replica tile kernel.
+// DIS many-replica tile kernel: O[d][r] = sum_k FK[d][k] F[r][k] over the
+// compacted (active flavour, x) index k, a plain product tiled 64 x 64 (data
+// points x replicas), the K range split over the grid's z dimension.
 // grid (ceil(ndata/64), ceil(R/64), nsplit); part[(split * R + r) * ndata + d]
 // ----------------------------------------------------------------------------
 template <typename T>
@@ -181,11 +186,10 @@ constexpr int TDT = 64, TRT = 64;
 
 template <typename T>
 constexpr size_t tile_smem() {
-    return sizeof(T) * (TileCfg<T>::KC * (TDT + 1) + TileCfg<T>::KC * TRT + 2 * MAX_NX * TRT) +
-           sizeof(int) * (2 * MAX_CH + MAX_NX);
+    return sizeof(T) * (TileCfg<T>::KC * (TDT + 1) + TileCfg<T>::KC * TRT) + sizeof(int) * (MAX_CH + MAX_NX);
 }
 
-template <int KIND, typename T>
+template <typename T>
 __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict__ fk,
                                               const T *__restrict__ F, int R, int nsplit,
                                               T *__restrict__ part) {
@@ -193,18 +197,12 @@ __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Bs = reinterpret_cast<T *>(smem_raw);  // [KC][TRT]
     T *As = Bs + KC * TRT;                    // [KC][TDT + 1]
-    T *Fa = As + KC * (TDT + 1);              // [nx][TRT]
-    T *Fb = Fa + MAX_NX * TRT;                // [nx][TRT]
-    int *sca = reinterpret_cast<int *>(Fb + MAX_NX * TRT);
-    int *scb = sca + MAX_CH;
-    int *sxm = scb + MAX_CH;
+    int *sfl = reinterpret_cast<int *>(As + KC * (TDT + 1));  // active flavours
+    int *sxm = sfl + MAX_CH;
 
     const int d0 = blockIdx.x * TDT, r0 = blockIdx.y * TRT, sp = blockIdx.z;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int k = threadIdx.x; k < tv.nch; k += 256) {
-        sca[k] = tv.ca[k];
-        if (KIND == FK_KIND_HAD) scb[k] = tv.cb[k];
-    }
+    for (int k = threadIdx.x; k < tv.nch; k += 256) sfl[k] = tv.ca[k];
     for (int k = threadIdx.x; k < tv.nx; k += 256) sxm[k] = tv.xmap[k];
 
     T acc[4][4];
@@ -214,85 +212,43 @@ __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict_
         for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
 
     const size_t fstride = (size_t)NFL * tv.nxg;
-    const int nx2 = tv.nx * tv.nx;
-    // Segments: hadronic = channels (nx*nx elements each); DIS = one segment of
-    // E elements whose range is split instead.
-    int seg_b, seg_e;
-    long long el_b = 0, el_e = 0;
-    if (KIND == FK_KIND_HAD) {
-        seg_b = (int)((long long)tv.nch * sp / nsplit);
-        seg_e = (int)((long long)tv.nch * (sp + 1) / nsplit);
-    } else {
-        seg_b = 0;
-        seg_e = 1;
-        const long long nk = (tv.E + KC - 1) / KC;
-        el_b = nk * sp / nsplit * KC;
-        el_e = min(tv.E, nk * (sp + 1) / nsplit * KC);
-    }
+    // this split's range of K, in whole KC chunks
+    const long long nk = (tv.E + KC - 1) / KC;
+    const long long el_b = nk * sp / nsplit * KC;
+    const long long el_e = min(tv.E, nk * (sp + 1) / nsplit * KC);
     __syncthreads();
-    for (int c = seg_b; c < seg_e; ++c) {
-        long long base, len;
-        if (KIND == FK_KIND_HAD) {
-            __syncthreads();
-            const int fa = sca[c], fb = scb[c];
-            for (int idx = threadIdx.x; idx < tv.nx * TRT; idx += 256) {
-                const int i = idx / TRT, rr = idx - i * TRT;
-                const int r = r0 + rr;
-                T va = T(0), vb = T(0);
-                if (r < R) {
-                    const T *Fr = F + (size_t)r * fstride;
-                    va = Fr[fa * tv.nxg + sxm[i]];
-                    vb = Fr[fb * tv.nxg + sxm[i]];
-                }
-                Fa[idx] = va;
-                Fb[idx] = vb;
-            }
-            __syncthreads();
-            base = (long long)c * nx2;
-            len = nx2;
-        } else {
-            base = el_b;
-            len = el_e - el_b;
+    for (long long k0 = el_b; k0 < el_e; k0 += KC) {
+        for (int idx = threadIdx.x; idx < KC * TDT; idx += 256) {
+            const int kk = idx % KC, dd = idx / KC;
+            const int d = d0 + dd;
+            T v = T(0);
+            if (d < tv.ndata && k0 + kk < el_e) v = fk[(size_t)d * tv.ldE + k0 + kk];
+            As[kk * (TDT + 1) + dd] = v;
         }
-        for (long long k0 = 0; k0 < len; k0 += KC) {
-            for (int idx = threadIdx.x; idx < KC * TDT; idx += 256) {
-                const int kk = idx % KC, dd = idx / KC;
-                const int d = d0 + dd;
-                T v = T(0);
-                if (d < tv.ndata && k0 + kk < len) v = fk[(size_t)d * tv.ldE + base + k0 + kk];
-                As[kk * (TDT + 1) + dd] = v;
+        for (int idx = threadIdx.x; idx < KC * TRT; idx += 256) {
+            const int rr = idx % TRT, kk = idx / TRT;
+            T v = T(0);
+            if (k0 + kk < el_e && r0 + rr < R) {
+                const int e = (int)(k0 + kk);
+                const int kf = e / tv.nx, i = e - kf * tv.nx;
+                v = F[(size_t)(r0 + rr) * fstride + sfl[kf] * tv.nxg + sxm[i]];
             }
-            for (int idx = threadIdx.x; idx < KC * TRT; idx += 256) {
-                const int rr = idx % TRT, kk = idx / TRT;
-                T v = T(0);
-                if (k0 + kk < len) {
-                    if (KIND == FK_KIND_HAD) {
-                        const int k = (int)(k0 + kk);
-                        const int i = k / tv.nx, j = k - (k / tv.nx) * tv.nx;
-                        v = Fa[i * TRT + rr] * Fb[j * TRT + rr];
-                    } else if (r0 + rr < R) {
-                        const int e = (int)(base + k0 + kk);
-                        const int kf = e / tv.nx, i = e - kf * tv.nx;
-                        v = F[(size_t)(r0 + rr) * fstride + sca[kf] * tv.nxg + sxm[i]];
-                    }
-                }
-                Bs[kk * TRT + rr] = v;
-            }
-            __syncthreads();
+            Bs[kk * TRT + rr] = v;
+        }
+        __syncthreads();
 #pragma unroll 4
-            for (int kk = 0; kk < KC; ++kk) {
-                T a[4], b[4];
+        for (int kk = 0; kk < KC; ++kk) {
+            T a[4], b[4];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) a[p] = As[kk * (TDT + 1) + ty * 4 + p];
+            for (int p = 0; p < 4; ++p) a[p] = As[kk * (TDT + 1) + ty * 4 + p];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = Bs[kk * TRT + tx * 4 + q];
+            for (int q = 0; q < 4; ++q) b[q] = Bs[kk * TRT + tx * 4 + q];
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
+            for (int p = 0; p < 4; ++p)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
-            }
-            __syncthreads();
+                for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
         }
+        __syncthreads();
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p)
@@ -815,24 +771,24 @@ int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, c
         k_stream<KIND, T><<<grid, 256, 0, s>>>(tv, fk, F, R, part);
         count_launch();
         FK_CUDA(cudaGetLastError());
-    } else if (KIND == FK_KIND_HAD) {
+    } else if constexpr (KIND == FK_KIND_HAD) {
         nparts = fac_nsplit(t);
         FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
         int rc = launch_fac<T>(t, F, R, fk, nparts, part, s);
         if (rc) return rc;
     } else {
         const int dt = (t->ndata + TDT - 1) / TDT, rt = (R + TRT - 1) / TRT;
-        const long long nseg = KIND == FK_KIND_HAD ? t->nch : (t->E + TileCfg<T>::KC - 1) / TileCfg<T>::KC;
+        const long long nseg = (t->E + TileCfg<T>::KC - 1) / TileCfg<T>::KC;
         // The split depends on the table only, so a replica's summation
         // order does not change with R (bit-exact batching of requests).
         long long want = (2LL * num_sms() + dt - 1) / dt;
         nparts = (int)std::max(1LL, std::min(nseg, want));
         FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
         constexpr size_t smem = tile_smem<T>();
-        int rc = set_smem<T>(k_tile<KIND, T>, smem);
+        int rc = set_smem<T>(k_tile<T>, smem);
         if (rc) return rc;
         dim3 grid(dt, rt, nparts);
-        k_tile<KIND, T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
+        k_tile<T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
         count_launch();
         FK_CUDA(cudaGetLastError());
     }

@@ -233,6 +233,44 @@ int fk_cov_size(const fk_cov *cov);
 int fk_chi2(const fk_cov *cov, const void *O, const double *D, int R, double *chi2, void *gO,
             int io_prec, fk_stream stream);
 
+/* ----------------------------------------------------- gradient descent */
+
+/*
+ * PDF parametrisation for the fit, which minimises chi^2 by gradient descent
+ * over the parameters of the PDFs (Sec. 2; the paper's parametrisation is a
+ * neural network, the analytic form below stands in for it).  Per replica r
+ * and flavour a:
+ *   f^r_a(x) = exp(t[r][a][0] + t[r][a][1] ln x + t[r][a][2] ln(1 - x)),
+ * i.e. A x^alpha (1 - x)^beta with t = (ln A, alpha, beta).
+ * theta: DEVICE [R][14][3]; x_grid: DEVICE [nx_grid] double, 0 < x < 1;
+ * F: DEVICE [R][14][nx_grid].  theta and F are double for FK_FP64 and float
+ * for any other mode; the exponent is evaluated in that type.
+ * Errors: FK_EINVAL.
+ */
+int fk_pdf_eval(const void *theta, int R, const double *x_grid, int nx_grid, void *F, int prec,
+                fk_stream stream);
+
+/*
+ * Chain rule through fk_pdf_eval:
+ *   gtheta[r][a][k] = sum_m gF[r][a][m] * dF[r][a][m] / dtheta[r][a][k],
+ * dF/dt0 = F, dF/dt1 = F ln x_m, dF/dt2 = F ln(1 - x_m), with F the output of
+ * fk_pdf_eval for the same theta.  F, gF: DEVICE [R][14][nx_grid]; gtheta:
+ * DEVICE [R][14][3]; types as for fk_pdf_eval.  The sum over the grid runs in
+ * a fixed order.  Errors: FK_EINVAL.
+ */
+int fk_pdf_grad(const void *F, const void *gF, int R, const double *x_grid, int nx_grid, void *gtheta,
+                int prec, fk_stream stream);
+
+/*
+ * One Adam step (Kingma and Ba) on n parameters, step number t >= 1:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * p, g, m, v: DEVICE, n elements of the mode's type (m and v start at 0 and
+ * are updated in place).  Errors: FK_EINVAL.
+ */
+int fk_adam_step(void *p, const void *g, void *m, void *v, long long n, int t, double lr, double b1,
+                 double b2, double eps, int prec, fk_stream stream);
+
 /* -------------------------------------------------------------- serving */
 
 /*

@@ -29,6 +29,10 @@ SIGNATURES = {
     "fk_cov_destroy": [P],
     "fk_cov_size": [P],
     "fk_chi2": [P, P, P, I, P, P, I, P],
+    "fk_pdf_eval": [P, I, P, I, P, I, P],
+    "fk_pdf_grad": [P, P, I, P, I, P, I, P],
+    "fk_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                     ctypes.c_double, I, P],
     "fk_serve_create": [SZ, I, PP],
     "fk_serve_add_table": [P, P, P],
     "fk_serve_submit": [P, I, P, I, I, ctypes.POINTER(U64)],

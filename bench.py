@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--waves", type=int, default=1, help="fit case: forward waves of the pipelined step")
     ap.add_argument("--streams", type=int, default=0,
                     help="fit case: streams the tables are spread over (0: one per table)")
-    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve"],
+    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
                          "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
-                         "serve: the served mixed workload (Poisson arrivals over 41 resident tables)")
+                         "serve: the served mixed workload (Poisson arrivals over 41 resident tables); "
+                         "descent: Adam on the PDF parameters of every replica, iterations of the fit")
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
@@ -489,6 +490,62 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_descent(args):
+    """Gradient descent on the PDF parameters of the R = 100 replicas over the
+    global set: per iteration, parametrisation -> pipelined fit step ->
+    parameter gradient -> Adam.  Replicas start from parameters jittered
+    around the ones the pseudo-data were drawn from; reports iterations per
+    second (as datapoint*replicas/s of the fit step they contain) and the
+    chi^2/ndata of the replicas before and after."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    from paper_1909_10547_b300.descent import PDFDescent
+    from paper_1909_10547_b300.fitstep import GlobalFit
+    g = workload()
+    tabs64 = [fk.Table.from_workload(t, ("fp64",)) for t in g.tables]
+    Ft = torch.tensor(g.F_true, device="cuda")
+    o_true = [fk.conv(t, Ft, "fp64")[0].cpu().numpy() for t in tabs64]
+    del tabs64
+    cov = W.covariance(o_true, SEED)
+    D = np.concatenate(W.pseudo_data(o_true, SEED))
+    rng = np.random.default_rng(SEED + 2)
+    t0 = np.empty((REPLICAS, 14, 3))
+    t0[..., 0] = np.log(g.params.A)[None, :] + rng.uniform(-0.3, 0.3, (REPLICAS, 14))
+    t0[..., 1] = g.params.alpha[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
+    t0[..., 2] = g.params.beta[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
+    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None)
+    fit.capture()
+    gd = PDFDescent(fit, t0, g.x, lr=0.02)
+    for _ in range(max(3, args.warmup)):
+        gd.step()
+    gd.__init__(fit, t0, g.x, lr=0.02)  # restart from t0 after the warm-up
+    torch.cuda.synchronize()
+    gd.step()
+    chi_first = fit.chi2.cpu().numpy().copy()
+    iters = max(args.steps, 200)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record()
+        for _ in range(iters):
+            gd.step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    chi_last = fit.chi2.cpu().numpy()
+    line = {"metric": METRIC, "value": fit.ntot * fit.R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": iters, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": dict(config_dict(g, args.prec), workload="gradient descent on the PDF parameters of "
+                           "100 replicas over the global-shaped set (one fit step per iteration)",
+                           optimizer="Adam, lr 0.02"),
+            "descent": {"chi2_per_point_first_median": float(np.median(chi_first) / fit.ntot),
+                        "chi2_per_point_last_median": float(np.median(chi_last) / fit.ntot),
+                        "iterations_timed": iters + 1},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import torch
@@ -497,6 +554,9 @@ def main():
         return
     if args.case == "serve":
         run_serve(args)
+        return
+    if args.case == "descent":
+        run_descent(args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

@@ -92,12 +92,20 @@ int fk_version(void);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads, all devices); for accounting in benchmarks. */
 uint64_t fk_kernel_launches(void);
-/* Device-side health of the tensor-core kernels on the current device: every
- * wait inside them (on a copy, an MMA or another warp) is bounded in time; if
+/* Device-side health of the current device: every wait inside the library's
+ * pipelined kernels (tensor-core convolution and adjoint, factorised CUDA-core
+ * convolution: waits on a copy, an MMA or another warp) is bounded in time; if
  * one ran out, the kernel stopped early, left its outputs incomplete and
  * raised a flag.  Returns FK_ETIMEDOUT if the flag is set, else FK_OK; clears
  * it if reset != 0.  Synchronises with the device (a blocking copy). */
 int fk_device_status(int reset);
+/* Check of that mechanism: launches one thread that waits, through the same
+ * bounded wait the tensor-core kernels use but with a limit of limit_us
+ * microseconds (1 .. 1000000), on a barrier nothing arrives on; the wait runs
+ * out, the kernel returns and raises the flag.  Synchronises with the device.
+ * Returns FK_OK if the flag was raised (and clears it; a flag set before the
+ * call is cleared too), FK_ECUDA otherwise.  The device stays usable. */
+int fk_wait_selftest(int limit_us);
 
 /* ---------------------------------------------------------------- tables */
 

@@ -16,6 +16,7 @@ PP = ctypes.POINTER(ctypes.c_void_p)
 SIGNATURES = {
     "fk_version": [],
     "fk_device_status": [I],
+    "fk_wait_selftest": [I],
     "fk_table_create_dis": [P, I, P, I, I, P, I, U, PP],
     "fk_table_create_had": [P, I, P, P, I, I, P, I, U, PP],
     "fk_table_destroy": [P],

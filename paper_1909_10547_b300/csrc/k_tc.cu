@@ -95,12 +95,13 @@ constexpr uint32_t SLEEP_NS = 100000;  // suspend-time hint per poll
 // the device error word; `dead` latches per thread, so after one time-out a
 // role stops waiting at once and the CTA drains within a few time-outs
 // instead of waiting on every remaining barrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, bool &dead) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, bool &dead,
+                                          uint64_t limit_ns = WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     if (dead) return false;
     const uint64_t t0 = gtimer();
     while (!mbar_try_sleep(bar, parity, SLEEP_NS)) {
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > limit_ns) {
             dead = true;
             atomicExch(&g_fk_device_error, 1);
             return false;
@@ -1319,6 +1320,19 @@ void tc_free(fk_table *t) {
     t->tc.gmap = nullptr;
 }
 
+namespace {
+// One thread waits on an mbarrier that expects one arrival nobody makes: the
+// bounded wait gives up after limit_ns and raises the device error word.
+__global__ void k_wait_selftest(uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool dead = false;
+    mbar_wait(b, 0, dead, limit_ns);
+}
+}  // namespace
+
 int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_cols,
                    int box_rows) {
     auto fn = encoder();
@@ -1346,3 +1360,18 @@ int device_status(int reset) {
 }
 
 }  // namespace fk
+
+int fk_wait_selftest(int limit_us) {
+    using namespace fk;
+    if (limit_us < 1 || limit_us > 1000000) return fail(FK_EINVAL, "fk_wait_selftest: limit_us in 1 .. 1000000");
+    int rc = device_status(1);  // start from a clear flag
+    if (rc != FK_OK && rc != FK_ETIMEDOUT) return rc;
+    k_wait_selftest<<<1, 1>>>((uint64_t)limit_us * 1000ull);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    FK_CUDA(cudaDeviceSynchronize());
+    rc = device_status(1);
+    if (rc == FK_ETIMEDOUT) return FK_OK;
+    if (rc != FK_OK) return rc;
+    return fail(FK_ECUDA, "fk_wait_selftest: the bounded wait did not report");
+}

@@ -209,7 +209,7 @@ def run_reference(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": config_dict(g, "fp64"),
+            "config": config_dict(g, "fp64", graphs=False),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -271,13 +271,15 @@ def roofline(fit, seg, prec):
             "phase_ms": seg}
 
 
-def config_dict(g, prec):
+def config_dict(g, prec, table_bytes=None, graphs=True):
     ntot = sum(t.ndata for t in g.tables)
+    elems = sum(t.fk.size for t in g.tables)
+    l2 = (f"inputs larger than L2 (resident FK tables {table_bytes / 1e9:.2f} GB on the device)"
+          if table_bytes else f"inputs larger than L2 ({elems / 1e6:.0f}M FK elements, {8 * elems / 1e9:.2f} GB in FP64)")
     return {"workload": "global-shaped chi2 fit step (forward + FP64 chi2 + adjoint): 40 datasets "
                         "(12 DIS, 28 hadronic), nx 20..50 on a 50-point grid, 20..120 channels",
             "ndata_total": ntot, "replicas": REPLICAS, "tables": len(g.tables), "prec": prec,
-            "l2": "inputs larger than L2 (resident FK tables ~1.4 GB FP32)",
-            "graphs": True, "parallelism": "replicas only (one independent copy per rank)"}
+            "l2": l2, "graphs": graphs, "parallelism": "replicas only (one independent copy per rank)"}
 
 
 def traffic_of(kernel, prec, ndata, replicas):
@@ -536,7 +538,8 @@ def run_descent(args):
     line = {"metric": METRIC, "value": fit.ntot * fit.R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": iters, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": dict(config_dict(g, args.prec), workload="gradient descent on the PDF parameters of "
+            "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)),
+                           workload="gradient descent on the PDF parameters of "
                            "100 replicas over the global-shaped set (one fit step per iteration)",
                            optimizer="Adam, lr 0.02"),
             "descent": {"chi2_per_point_first_median": float(np.median(chi_first) / fit.ntot),
@@ -637,7 +640,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16",
                                            "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
-            "data": "synthetic", "config": dict(config_dict(g, args.prec), streams=fit.nstreams,
+            "data": "synthetic",
+            "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
                                                schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves"),
             "roofline": roof,
             "e2e": {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT,

@@ -226,9 +226,10 @@ def test_replica_result_independent_of_batch(prec):
     full = run_conv(tab, F, prec)
     part = run_conv(tab, F[37:37 + 64], prec)
     assert np.array_equal(full[37:37 + 64], part)
-    small = run_conv(tab, F[5:8], prec)
+    small = run_conv(tab, F[5:8], prec)       # replica tile of 16 instead of 64 (32 in FP64)
     again = run_conv(tab, F[5:8], prec)
     assert np.array_equal(small, again)
+    assert np.array_equal(full[5:8], small)
 
 
 # ---------------------------------------------------------------- errors ----

@@ -283,13 +283,19 @@ def config_dict(g, prec, table_bytes=None, graphs=True):
 
 
 def traffic_of(kernel, prec, ndata, replicas):
-    """DRAM bytes per launch of `kernel` for this stress workload, from the
-    committed ncu capture list (profiles/dram_traffic.txt), or None when no
-    capture matches or the kernel's source has changed since it was taken."""
-    src = {"k_tc": "k_tc.cu", "k_stream": "k_cc.cu", "k_fac": "k_cc.cu"}[kernel]
+    """DRAM bytes per launch of `kernel` (per step for "fit_step": all the
+    step's kernels) for this workload, from the committed ncu capture list
+    (profiles/dram_traffic.txt), or None when no capture matches or the
+    source has changed since it was taken."""
     here = os.path.dirname(os.path.abspath(__file__))
-    with open(os.path.join(here, "paper_1909_10547_b300", "csrc", src), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    csrc = os.path.join(here, "paper_1909_10547_b300", "csrc")
+    srcs = ({"k_tc": ["k_tc.cu"], "k_stream": ["k_cc.cu"], "k_fac": ["k_cc.cu"]}.get(kernel) or
+            sorted(f for f in os.listdir(csrc) if f.endswith(".cu")))
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(csrc, src), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
     try:
         lines = open(os.path.join(here, "profiles", "dram_traffic.txt")).read().splitlines()
     except OSError:
@@ -635,6 +641,8 @@ def main():
     units = fit.ntot * fit.R
     value = units * world / (ms * 1e-3)
     roof = roofline(fit, seg, args.prec)
+    if "step" in seg:
+        roof["traffic"] = traffic_of("fit_step", args.prec, fit.ntot, fit.R)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

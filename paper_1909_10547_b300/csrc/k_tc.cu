@@ -293,6 +293,7 @@ __host__ __device__ constexpr int tc_stages() {
 
 struct TcParams {
     int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
+    int nbl;  // log2 of the TMEM accumulator buffers (2 of 256 columns or 4 of 128)
     int kbeg[NFL], kend[NFL];
     const float *Fm;  // forward: [ngroups][nx][R_pad] epilogue multipliers f^r_{a_g}(x_i)
     float *O;         // forward: observables, row stride ldo
@@ -356,9 +357,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 8u * (S + s); };
     auto accf = [&](int b) { return bar0 + 8u * (2 * S + b); };
-    auto acce = [&](int b) { return bar0 + 8u * (2 * S + 2 + b); };
-    const uint32_t drain = bar0 + 8u * (2 * S + 4);  // all MMAs of this CTA done
-    uint8_t *gen = smem_raw + (bar0 - raw) + 8 * (2 * S + 5);
+    auto acce = [&](int b) { return bar0 + 8u * (2 * S + 4 + b); };
+    const uint32_t drain = bar0 + 8u * (2 * S + 8);  // all MMAs of this CTA done
+    uint8_t *gen = smem_raw + (bar0 - raw) + 8 * (2 * S + 9);
+    // accumulator buffers: NB = 1 << nbl of bcols TMEM columns each; use u of
+    // the accumulator is buffer u & NBM, phase u >> nbl of its barriers
+    const int nbl = p.nbl, NB = 1 << nbl, NBM = NB - 1;
+    const uint32_t bcols = 512u >> nbl;
     volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(gen);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < 4; ++b) {
             mbar_init(accf(b), 1);
             mbar_init(acce(b), 4 * CL);  // the epilogue warps of every CTA of the pair
         }
@@ -390,21 +395,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // Accumulator hand-off.  Use u of the double-buffered accumulator may
-    // start once the epilogue has released use u - 2 (the same buffer).  For
+    // Accumulator hand-off.  Use u of the NB-buffered accumulator may
+    // start once the epilogue has released use u - NB (the same buffer).  For
     // group g that wait is made by the (even CTA's) producer before it loads
     // the stage holding the group's first K step: the MMAs reach that stage
     // only through its full barrier, so they are ordered after the release,
     // and the MMA thread itself does not wait on the epilogue.  The producer
     // runs S stages ahead of the MMAs, so it takes the wait only where use
-    // u - 2 ends at least S + PW_SLACK stages before that stage (in this tile
-    // or an earlier one): then the release is due and the wait costs nothing,
-    // and use u - 2 needs no stage the producer has yet to load.  For groups
+    // u - NB ends at least S + PW_SLACK stages before that stage (in this
+    // tile or an earlier one): then the release is due and the wait costs
+    // nothing, and use u - NB needs no stage the producer has yet to load.  For groups
     // that follow closer behind (short groups), the MMA thread waits at the
     // group's first K step, with the stage already loaded.
     uint32_t pwait = 0;
     for (int g = 0; g < p.ngroups; ++g) {
-        int u2 = g - 2, back = 0;  // group of use u - 2, tiles back
+        int u2 = g - NB, back = 0;  // group of use u - NB, tiles back
         while (u2 < 0) {
             u2 += p.ngroups;
             ++back;
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // the accumulator of every group starting in this stage
                     // must be free before the MMAs can read the stage
                     while (pg < p.ngroups && p.kbeg[pg] < (q + 1) * T::KCS) {
-                        if (((pwait >> pg) & 1u) && !mbar_wait(acce(pgc & 1), ((pgc >> 1) & 1) ^ 1, dead)) {
+                        if (((pwait >> pg) & 1u) && !mbar_wait(acce(pgc & NBM), ((pgc >> nbl) & 1) ^ 1, dead)) {
                             ok = false;
                             break;
                         }
@@ -528,8 +533,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
                         if (g >= p.ngroups) break;  // K padding after the last group
-                        const int b = gc & 1;
-                        const uint32_t d = tmem + (uint32_t)(b * 256);
+                        const int b = gc & NBM;
+                        const uint32_t d = tmem + (uint32_t)b * bcols;
                         // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
                         const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
@@ -559,15 +564,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
                         if (g >= p.ngroups) break;
-                        const int b = gc & 1;
+                        const int b = gc & NBM;
                         if (k == kb && ((mwait >> g) & 1u)) {
-                            if (!mbar_wait(acce(b), ((gc >> 1) & 1) ^ 1, dead)) {
+                            if (!mbar_wait(acce(b), ((gc >> nbl) & 1) ^ 1, dead)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
                         }
-                        const uint32_t d = tmem + (uint32_t)(b * 256);
+                        const uint32_t d = tmem + (uint32_t)b * bcols;
                         // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
                         const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int ncols = G * p.nx;      // accumulator columns in use: column i * G + dl
             constexpr int MI = 255 / G + 1;  // x points a 256-column accumulator can hold
             for (int g = 0; g < p.ngroups; ++g, ++gc) {
-                const int b = gc & 1;
+                const int b = gc & NBM;
                 // the multipliers f^r_{a_g}(x_i) do not depend on the MMA:
                 // fetch them all before waiting so their latency overlaps it
                 float m[MODE == MODE_FWD ? MI : 1];
@@ -648,14 +653,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 // one lane waits, the warp follows (tcgen05.ld is warp-collective)
                 int got = 1;
-                if (lane == 0) got = mbar_wait(accf(b), (gc >> 1) & 1, dead);
+                if (lane == 0) got = mbar_wait(accf(b), (gc >> nbl) & 1, dead);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * bcols;
                 // adjoint: per x point, the sum over the tile's data points
                 float ps[MODE == MODE_ADJ ? MI : 1];
                 if (MODE == MODE_ADJ) {
@@ -1082,6 +1087,10 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     p.ntiles = L.ntile_n * p.nrt;
     p.nchunks = pk.ktot_pad / Tr<PREC>::KCS;
     p.n_rows = L.n_rows;
+    // narrow tiles (G * nx <= 128, i.e. nx <= 8) keep four accumulators of 128
+    // TMEM columns in flight instead of two of 256, so the short channel
+    // groups of such tables wait less on the epilogue
+    p.nbl = L.n_rows <= 128 ? 2 : 1;
     p.ngroups = pk.grp.ngroups;
     p.nx = t->nx;
     p.ndata = t->ndata;

@@ -295,6 +295,7 @@ struct TcParams {
     int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
     int nbl;  // log2 of the TMEM accumulator buffers (2 of 256 columns or 4 of 128)
     int kbeg[NFL], kend[NFL];
+    uint32_t pwait;   // bit g: the producer makes group g's accumulator wait (tc_pwait)
     const float *Fm;  // forward: [ngroups][nx][R_pad] epilogue multipliers f^r_{a_g}(x_i)
     float *O;         // forward: observables, row stride ldo
     const float *gO;  // adjoint: weights gO[r * ldo + d]
@@ -395,28 +396,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // Accumulator hand-off.  Use u of the NB-buffered accumulator may
-    // start once the epilogue has released use u - NB (the same buffer).  For
-    // group g that wait is made by the (even CTA's) producer before it loads
-    // the stage holding the group's first K step: the MMAs reach that stage
-    // only through its full barrier, so they are ordered after the release,
-    // and the MMA thread itself does not wait on the epilogue.  The producer
-    // runs S stages ahead of the MMAs, so it takes the wait only where use
-    // u - NB ends at least S + PW_SLACK stages before that stage (in this
-    // tile or an earlier one): then the release is due and the wait costs
-    // nothing, and use u - NB needs no stage the producer has yet to load.  For groups
-    // that follow closer behind (short groups), the MMA thread waits at the
-    // group's first K step, with the stage already loaded.
-    uint32_t pwait = 0;
-    for (int g = 0; g < p.ngroups; ++g) {
-        int u2 = g - NB, back = 0;  // group of use u - NB, tiles back
-        while (u2 < 0) {
-            u2 += p.ngroups;
-            ++back;
-        }
-        const int e2 = (p.kend[u2] + T::KCS - 1) / T::KCS - back * p.nchunks;  // stage after its last
-        if (p.kbeg[g] / T::KCS - S - e2 >= PW_SLACK) pwait |= 1u << g;
-    }
+    // groups whose accumulator hand-off the producer takes (tc_pwait)
+    const uint32_t pwait = p.pwait;
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------ TMA producer
@@ -501,13 +482,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0 && leader) {
         // ------------------------------------------------ MMA issuer
-        // The tensor pipe is fed best by straight-line MMA issue: a stage in
-        // which no group needs the MMA thread to wait for the epilogue runs a
-        // branch-light path; only stages where such a (short) group starts
-        // take the path with the wait.
+        // The tensor pipe is fed best by straight-line MMA issue: the K steps
+        // of a stage are unrolled, and a stage in which no group needs the
+        // MMA thread to wait for the epilogue runs a loop without any wait
+        // code; only stages where such a (short) group starts take the loop
+        // with the wait.
         const uint32_t idesc = (1u << 4) | (T::FMT << 7) | (T::FMT << 10) |
                                ((uint32_t)(p.n_rows >> 3) << 17) | ((uint32_t)((CL * TC_M) >> 4) << 24);
         const uint32_t mwait = ~pwait & ((1u << p.ngroups) - 1u);  // groups the MMA thread waits for
+        constexpr int SLOW_UNROLL = T::X3 ? 1 : T::KCS / T::KSTEP;
         // K index where the first MMA-waited group at or after group h starts
         auto next_wait_k = [&](int h) -> int {
             const uint32_t m = h < 32 ? mwait >> h : 0u;
@@ -529,6 +512,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t st = base + s * stage_bytes;
                 if (kw >= (q + 1) * T::KCS) {
+                    // no group of this stage needs the MMA thread to wait
 #pragma unroll
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
@@ -561,16 +545,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                     }
                 } else {
+                    // a group whose accumulator the MMA thread waits for
+                    // starts in this stage: the same pass with the wait at
+                    // that group's first K step (k == kw); unrolled except
+                    // for hi+lo, whose three MMAs per step make it large
+#pragma unroll SLOW_UNROLL
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
-                        if (g >= p.ngroups) break;
+                        if (g >= p.ngroups) break;  // K padding after the last group
                         const int b = gc & NBM;
-                        if (k == kb && ((mwait >> g) & 1u)) {
+                        if (k == kw) {  // first K step of a group the MMA thread waits for
                             if (!mbar_wait(acce(b), ((gc >> nbl) & 1) ^ 1, dead)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
+                            kw = next_wait_k(g + 1);
                         }
                         const uint32_t d = tmem + (uint32_t)b * bcols;
                         // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
@@ -598,9 +588,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                         }
                     }
-                    // the next wait is at a group that has not started yet:
-                    // group g itself if it begins at the next stage
-                    kw = next_wait_k(g < p.ngroups && kb >= (q + 1) * T::KCS ? g : g + 1);
                 }
                 if (CL == 2)
                     mma_commit_pair(empty(s));
@@ -995,11 +982,42 @@ BMaps b_maps(const TcPack &pk) {
     return {&pk.map_hi, &pk.map_hi, &pk.half_hi, &pk.half_hi};
 }
 
+// Accumulator hand-off.  Use u of the NB-buffered accumulator (one use per
+// channel group, counted across the CTA's tiles) may start once the epilogue
+// has released use u - NB, the same buffer.  For group g that wait is made by
+// the (even CTA's) producer before it loads the stage holding the group's
+// first K step: the MMAs reach that stage only through its full barrier, so
+// they are ordered after the release, and the MMA thread itself does not wait
+// on the epilogue.  The producer runs S stages ahead of the MMAs, so it takes
+// the wait only where use u - NB ends at least S + PW_SLACK stages before that
+// stage (in this tile or an earlier one): then the release is due and the
+// wait costs nothing, and use u - NB needs no stage the producer has yet to
+// load.  For groups that follow closer behind (short groups), the MMA thread
+// waits at the group's first K step, with the stage already loaded.  Returns
+// the mask of producer-side groups; it depends only on the table's packing
+// and the pipeline shape, so it is computed here once per launch.
+uint32_t tc_pwait(const TcParams &p, int S, int KCS) {
+    const int NB = 1 << p.nbl;
+    uint32_t pwait = 0;
+    for (int g = 0; g < p.ngroups; ++g) {
+        int u2 = g - NB, back = 0;  // group of use u - NB, tiles back
+        while (u2 < 0) {
+            u2 += p.ngroups;
+            ++back;
+        }
+        const int e2 = (p.kend[u2] + KCS - 1) / KCS - back * p.nchunks;  // stage after its last
+        if (p.kbeg[g] / KCS - S - e2 >= PW_SLACK) pwait |= 1u << g;
+    }
+    return pwait;
+}
+
 template <int PREC, int G, int MODE>
 int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const BMaps &mb,
-              const TcParams &p, cudaStream_t s) {
+              const TcParams &p0, cudaStream_t s) {
+    TcParams p = p0;
     // CTA pairs (256-row MMAs on two SMs) whenever the replica tiles pair up
     if (p.nrt % 2 == 0) {
+        p.pwait = tc_pwait(p, tc_stages<PREC, 2>(), Tr<PREC>::KCS);
         auto kern = k_tc<PREC, G, MODE, 2>;
         const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(t->tc.n_rows));
         // opt in once at the largest tile (n_rows = 256) so that every table fits
@@ -1024,6 +1042,7 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
             return FK_OK;
         }
     }
+    p.pwait = tc_pwait(p, tc_stages<PREC, 1>(), Tr<PREC>::KCS);
     auto kern = k_tc<PREC, G, MODE, 1>;
     int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;

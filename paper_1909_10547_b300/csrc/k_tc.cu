@@ -169,14 +169,20 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128 B,
 // 8-row groups 1024 B apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;   // SBO
-    d |= (uint64_t)1 << 46;             // version
-    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-    return d;
+__host__ __device__ constexpr uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4)  // start address, 16-byte units
+           | (uint64_t)1 << 16                  // LBO (unused for swizzled K-major)
+           | (uint64_t)(1024 >> 4) << 32        // SBO
+           | (uint64_t)1 << 46                  // version
+           | (uint64_t)2 << 61;                 // SWIZZLE_128B
 }
+// The same descriptor in two words: desc_lo (start address and LBO) varies
+// per operand and K step, DESC_HI (SBO, version, swizzle) is shared.
+constexpr uint32_t DESC_HI = (uint32_t)(sw128_desc(0) >> 32);
+__host__ __device__ constexpr uint32_t desc_lo(uint32_t addr) { return (uint32_t)sw128_desc(addr); }
+__host__ __device__ constexpr uint64_t desc64(uint32_t lo) { return ((uint64_t)DESC_HI << 32) | lo; }
+static_assert(desc64(desc_lo(0x2A7C0u)) == sw128_desc(0x2A7C0u), "descriptor split");
+static_assert(desc_lo(0x2A7C0u) + 0x403u == desc_lo(0x2A7C0u + 0x4030u), "a K-step offset adds to the address field");
 // D[tmem] (+)= A * B^T for one K step.  CG = 1: M = 128 rows of this CTA.
 // CG = 2 (issued by the even CTA of a pair): M = 256, rows 0..127 from the even
 // CTA's A and rows 128..255 from the odd CTA's A at the same shared-memory
@@ -496,6 +502,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t m = h < 32 ? mwait >> h : 0u;
             return m ? p.kbeg[h + __ffs(m) - 1] : 0x7fffffff;
         };
+        // The issue loop does little besides issuing: the stage's descriptors
+        // are built once per stage and a K step only adds its offset to the
+        // start-address field (16-byte units; shared-memory addresses stay
+        // below 256 KB, so the 14-bit field never carries), and the
+        // accumulator address changes only when a group ends.
+        const uint32_t bstep = b_bytes >> 4;           // one B atom, descriptor units
+        constexpr uint32_t ASTEP = (TC_M * 128) >> 4;  // one A atom
+        const int ng = p.ngroups;
+        const int klast = p.kend[ng - 1];  // K after the last group
         int it = 0, gc = 0;
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
@@ -503,6 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // arrays are read only when a group ends
             int g = 0, kb = p.kbeg[0], ke = p.kend[0];
             int kw = next_wait_k(0);
+            uint32_t d = tmem + (uint32_t)(gc & NBM) * bcols;
             for (int q = 0; q < p.nchunks && ok; ++q, ++it) {
                 const int s = it % S;
                 if (!mbar_wait(full(s), (it / S) & 1, dead)) {
@@ -511,34 +527,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t st = base + s * stage_bytes;
+                const uint32_t a0 = desc_lo(st), b0 = desc_lo(st + offB);
+                const uint32_t a20 = T::X3 ? desc_lo(st + offA2) : 0u, b20 = T::X3 ? desc_lo(st + offB2) : 0u;
                 if (kw >= (q + 1) * T::KCS) {
                     // no group of this stage needs the MMA thread to wait
 #pragma unroll
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
-                        if (g >= p.ngroups) break;  // K padding after the last group
-                        const int b = gc & NBM;
-                        const uint32_t d = tmem + (uint32_t)b * bcols;
-                        // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
+                        if (k >= klast) break;  // K padding after the last group
+                        // K step ks: atom ks / (KC / KSTEP), 32 bytes (2 descriptor units) per step within it
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
-                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
-                        const uint64_t ah = sw128_desc(st + atom * a_bytes + off);
-                        const uint64_t bh = sw128_desc(st + offB + atom * b_bytes + off);
-                        mma<PREC, CL>(d, ah, bh, idesc, k != kb);
+                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 2u;
+                        const uint32_t ao = atom * ASTEP + off, bo = atom * bstep + off;
+                        mma<PREC, CL>(d, desc64(a0 + ao), desc64(b0 + bo), idesc, k != kb);
                         if (T::X3) {
-                            const uint64_t al = sw128_desc(st + offA2 + atom * a_bytes + off);
-                            const uint64_t bl = sw128_desc(st + offB2 + atom * b_bytes + off);
-                            mma<PREC, CL>(d, ah, bl, idesc, 1);
-                            mma<PREC, CL>(d, al, bh, idesc, 1);
+                            mma<PREC, CL>(d, desc64(a0 + ao), desc64(b20 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64(a20 + ao), desc64(b0 + bo), idesc, 1);
                         }
                         if (k + T::KSTEP == ke) {
                             if (CL == 2)
-                                mma_commit_pair(accf(b));
+                                mma_commit_pair(accf(gc & NBM));
                             else
-                                mma_commit<1>(accf(b));
+                                mma_commit<1>(accf(gc & NBM));
                             ++gc;
                             ++g;
-                            if (g < p.ngroups) {
+                            d = tmem + (uint32_t)(gc & NBM) * bcols;
+                            if (g < ng) {
                                 kb = p.kbeg[g];
                                 ke = p.kend[g];
                             }
@@ -552,37 +566,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll SLOW_UNROLL
                     for (int ks = 0; ks < T::KCS / T::KSTEP; ++ks) {
                         const int k = q * T::KCS + ks * T::KSTEP;
-                        if (g >= p.ngroups) break;  // K padding after the last group
-                        const int b = gc & NBM;
+                        if (k >= klast) break;  // K padding after the last group
                         if (k == kw) {  // first K step of a group the MMA thread waits for
-                            if (!mbar_wait(acce(b), ((gc >> nbl) & 1) ^ 1, dead)) {
+                            if (!mbar_wait(acce(gc & NBM), ((gc >> nbl) & 1) ^ 1, dead)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
                             kw = next_wait_k(g + 1);
                         }
-                        const uint32_t d = tmem + (uint32_t)b * bcols;
-                        // K step ks: atom ks / (KC / KSTEP), 32 bytes per step within it
+                        // K step ks: atom ks / (KC / KSTEP), 32 bytes (2 descriptor units) per step within it
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
-                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 32u;
-                        const uint64_t ah = sw128_desc(st + atom * a_bytes + off);
-                        const uint64_t bh = sw128_desc(st + offB + atom * b_bytes + off);
-                        mma<PREC, CL>(d, ah, bh, idesc, k != kb);
+                        const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 2u;
+                        const uint32_t ao = atom * ASTEP + off, bo = atom * bstep + off;
+                        mma<PREC, CL>(d, desc64(a0 + ao), desc64(b0 + bo), idesc, k != kb);
                         if (T::X3) {
-                            const uint64_t al = sw128_desc(st + offA2 + atom * a_bytes + off);
-                            const uint64_t bl = sw128_desc(st + offB2 + atom * b_bytes + off);
-                            mma<PREC, CL>(d, ah, bl, idesc, 1);
-                            mma<PREC, CL>(d, al, bh, idesc, 1);
+                            mma<PREC, CL>(d, desc64(a0 + ao), desc64(b20 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64(a20 + ao), desc64(b0 + bo), idesc, 1);
                         }
                         if (k + T::KSTEP == ke) {
                             if (CL == 2)
-                                mma_commit_pair(accf(b));
+                                mma_commit_pair(accf(gc & NBM));
                             else
-                                mma_commit<1>(accf(b));
+                                mma_commit<1>(accf(gc & NBM));
                             ++gc;
                             ++g;
-                            if (g < p.ngroups) {
+                            d = tmem + (uint32_t)(gc & NBM) * bcols;
+                            if (g < ng) {
                                 kb = p.kbeg[g];
                                 ke = p.kend[g];
                             }

@@ -10,6 +10,8 @@ Functions (all FP64, numpy in / numpy out):
   had(table, F)            -> (O, S)   hadronic observables, Eq. 1
   dis_grad(table, gO)      -> gF       sum_d gO[r,d] dO[r,d]/dF[r,a,x]
   had_grad(table, F, gO)   -> gF       the same for Eq. 1 (product rule)
+  luminosity(table, F)     -> L        the PDF matrix of Table 3, L[r][(c,i,j)] = f_a(x_i) f_b(x_j)
+  dense(fk2d, L)           -> (O, S)   the dense product of Table 3, O[r][d] = sum_k fk[d][k] L[r][k]
   cholesky(C)              -> L        C = L L^T
   chi2(L, O, D)            -> (chi2, gO)  (O-D)^T C^-1 (O-D) and its O-gradient
 S is the sum of |terms| of each observable (the scale of its rounding error).
@@ -35,10 +37,13 @@ def lib():
         L.fk_oracle_had.argtypes = [I, I, P, P, I, P, P, I, I, P, P, P]
         L.fk_oracle_dis_grad.argtypes = [I, I, P, P, I, I, P, P]
         L.fk_oracle_had_grad.argtypes = [I, I, P, P, I, P, P, I, I, P, P, P]
+        L.fk_oracle_luminosity.argtypes = [I, P, P, I, P, I, I, P, P]
+        L.fk_oracle_dense.argtypes = [I, ctypes.c_longlong, P, I, P, P, P]
         L.fk_oracle_cholesky.argtypes = [I, P, P]
         L.fk_oracle_chi2.argtypes = [I, P, I, P, P, P, P]
         for f in (L.fk_oracle_dis, L.fk_oracle_had, L.fk_oracle_dis_grad,
-                  L.fk_oracle_had_grad, L.fk_oracle_cholesky, L.fk_oracle_chi2,
+                  L.fk_oracle_had_grad, L.fk_oracle_luminosity, L.fk_oracle_dense,
+                  L.fk_oracle_cholesky, L.fk_oracle_chi2,
                   L.fk_oracle_threads):
             f.restype = I
         _lib = L
@@ -126,6 +131,31 @@ def conv(t, F):
 
 def conv_grad(t, F, gO):
     return had_grad(t, F, gO) if hasattr(t, "ca") else dis_grad(t, gO)
+
+
+def luminosity(t, F):
+    """The PDF matrix of Table 3 for a HadTable-like t: [R][nc * nx * nx]."""
+    F = _f64(F)
+    R = F.shape[0]
+    nc, nx = len(t.ca), len(t.xmap)
+    assert F.shape[1:] == (14, t.nxg)
+    ca, cb, xm = _i32(t.ca), _i32(t.cb), _i32(t.xmap)
+    L = np.empty((R, nc * nx * nx))
+    _check(lib().fk_oracle_luminosity(nc, _p(ca), _p(cb), nx, _p(xm), t.nxg, R, _p(F), _p(L)), "luminosity")
+    return L
+
+
+def dense(fk, L):
+    """fk [ndata][K], L [R][K] (the PDF matrix, replica-major) -> (O [R][ndata], S)."""
+    fk = _f64(fk)
+    L = _f64(L)
+    nd, K = fk.shape
+    R = L.shape[0]
+    assert L.shape[1] == K
+    O = np.empty((R, nd))
+    S = np.empty((R, nd))
+    _check(lib().fk_oracle_dense(nd, K, _p(fk), R, _p(L), _p(O), _p(S)), "dense")
+    return O, S
 
 
 def cholesky(C):

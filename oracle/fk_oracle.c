@@ -244,6 +244,57 @@ int fk_oracle_chi2(int n, const double *L, int R, const double *O, const double 
     return 0;
 }
 
+/*
+ * The "PDF matrix" of the paper's timing study (Sec. 3, Table 3): for a
+ * hadronic channel list, one column per replica holding the products
+ * f_a(x_i) f_b(x_j) in the table's (channel, x_i, x_j) element order, so that
+ * Eq. 1 becomes a plain product of the flattened table with this matrix.
+ * Stored replica-major: L[r][(c * nx + i) * nx + j] = F[r][ca[c]][xmap[i]] * F[r][cb[c]][xmap[j]].
+ */
+int fk_oracle_luminosity(int nc, const int *ca, const int *cb, int nx, const int *xmap, int nxg,
+                         int R, const double *F, double *L)
+{
+    if (nc < 0 || nx < 0 || R < 0 || check_xmap(xmap, nx, nxg)) return -1;
+    for (int c = 0; c < nc; ++c)
+        if (ca[c] < 0 || ca[c] >= NFL || cb[c] < 0 || cb[c] >= NFL) return -1;
+    const size_t K = (size_t)nc * nx * nx;
+    for (int r = 0; r < R; ++r) {
+        const double *f = F + (size_t)r * NFL * nxg;
+        for (int c = 0; c < nc; ++c)
+            for (int i = 0; i < nx; ++i)
+                for (int j = 0; j < nx; ++j)
+                    L[(size_t)r * K + ((size_t)c * nx + i) * nx + j] =
+                        f[ca[c] * nxg + xidx(xmap, i)] * f[cb[c] * nxg + xidx(xmap, j)];
+    }
+    return 0;
+}
+
+/*
+ * The dense product timed in the paper's Table 3: an FK table flattened to
+ * [ndata][K] times a PDF matrix [K][R] (given replica-major, L[r][k]):
+ *   O[r][d] = sum_k fk[d][k] * L[r][k],  S[r][d] = sum_k |fk[d][k] * L[r][k]|.
+ */
+int fk_oracle_dense(int ndata, long long K, const double *fk, int R, const double *L,
+                    double *O, double *S)
+{
+    if (ndata < 0 || K < 0 || R < 0) return -1;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int r = 0; r < R; ++r)
+        for (int d = 0; d < ndata; ++d) {
+            const double *row = fk + (size_t)d * K;
+            const double *l = L + (size_t)r * K;
+            acc_t o = {0, 0}, s = {0, 0};
+            for (long long k = 0; k < K; ++k) {
+                const double term = row[k] * l[k];
+                acc_add(&o, term);
+                acc_add(&s, fabs(term));
+            }
+            O[(size_t)r * ndata + d] = acc_get(&o);
+            if (S) S[(size_t)r * ndata + d] = acc_get(&s);
+        }
+    return 0;
+}
+
 /* Threads the OpenMP runtime will use (for reporting the CPU baseline). */
 int fk_oracle_threads(void)
 {

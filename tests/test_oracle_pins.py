@@ -392,3 +392,60 @@ def test_chi2_gradient_is_exact_central_difference():
         e[0, k] = 0.5
         fd = (oracle.chi2(L, O + e, D, False)[0] - oracle.chi2(L, O - e, D, False)[0]) / 1.0
         assert abs(fd[0] - g[0, k]) <= 1e-11 * np.abs(g).max()
+
+
+# ------------------------------------------- dense product (Table 3) ----
+
+def test_dense_exact_bruteforce():
+    """The dense product of the paper's Table 3 on small integers, against a
+    rational brute-force sum written from its definition."""
+    rng = np.random.default_rng(11)
+    nd, K, R = 4, 37, 3
+    fk = rng.integers(-5, 6, (nd, K)).astype(np.float64)
+    L = rng.integers(-5, 6, (R, K)).astype(np.float64)
+    O, S = oracle.dense(fk, L)
+    for r in range(R):
+        for d in range(nd):
+            want = sum(Fraction(int(fk[d, k])) * Fraction(int(L[r, k])) for k in range(K))
+            assert O[r, d] == float(want)
+            assert S[r, d] == float(sum(abs(Fraction(int(fk[d, k])) * Fraction(int(L[r, k]))) for k in range(K)))
+
+
+def test_dense_one_hot_selects_columns():
+    """A PDF matrix whose replica r is the unit vector e_{k_r} returns column
+    k_r of the table: catches a transposed operand or a shifted index."""
+    rng = np.random.default_rng(12)
+    nd, K = 5, 23
+    fk = rng.standard_normal((nd, K))
+    ks = [0, 7, 22, 13]
+    L = np.zeros((len(ks), K))
+    for r, k in enumerate(ks):
+        L[r, k] = 1.0
+    O, _ = oracle.dense(fk, L)
+    for r, k in enumerate(ks):
+        assert np.array_equal(O[r], fk[:, k])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_dense_of_luminosity_is_eq1_exactly(seed):
+    """Table 3's formulation (flattened table times the PDF matrix) and Eq. 1
+    (the per-channel quadratic form) are the same sum in different orders; on
+    integer inputs both are exact, so they must agree bit for bit, and the
+    PDF matrix must hold f_a(x_i) f_b(x_j) at element (c, i, j)."""
+    t, F = _tiny_int_had(seed)
+    L = oracle.luminosity(t, F)
+    nc, nx = len(t.ca), len(t.xmap)
+    r, c, i, j = 1, 2, 0, 2
+    assert L[r, (c * nx + i) * nx + j] == F[r, t.ca[c], t.xmap[i]] * F[r, t.cb[c], t.xmap[j]]
+    Od, Sd = oracle.dense(t.fk.reshape(t.fk.shape[0], -1), L)
+    Oh, Sh = oracle.had(t, F)
+    assert np.array_equal(Od, Oh) and np.array_equal(Sd, Sh)
+
+
+def test_dense_of_luminosity_matches_eq1_on_config1():
+    """Same identity on the config-1 table with real-valued PDFs: the two
+    orders of summation agree within a few units of rounding of S."""
+    t, F = W.config1(R=3)
+    Od, Sd = oracle.dense(t.fk.reshape(t.fk.shape[0], -1), oracle.luminosity(t, F))
+    Oh, Sh = oracle.had(t, F)
+    assert np.abs(Od - Oh).max() <= 1e-15 * Sh.max()

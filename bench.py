@@ -46,18 +46,21 @@ def parse():
     ap.add_argument("--waves", type=int, default=1, help="fit case: forward waves of the pipelined step")
     ap.add_argument("--streams", type=int, default=0,
                     help="fit case: streams the tables are spread over (0: one per table)")
-    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent"],
+    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent", "dense"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
                          "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
                          "serve: the served mixed workload (Poisson arrivals over 41 resident tables); "
-                         "descent: Adam on the PDF parameters of every replica, iterations of the fit")
+                         "descent: Adam on the PDF parameters of every replica, iterations of the fit; "
+                         "dense: the paper's Table 3 product FK[ndata x 35721] . PDF[35721 x R] "
+                         "(--ndata, --replicas; default 2000 x 2000)")
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
     ap.add_argument("--table", default="stress", choices=["stress", "config1"],
                     help="stress case: the stress table, or the plain hadronic table of configs 1-2 "
                          "(200 data points, 60 channels, nx = 30; R = 512 is config 2)")
-    ap.add_argument("--replicas", type=int, default=1, help="stress case: replicas")
+    ap.add_argument("--replicas", type=int, default=None,
+                    help="stress case: replicas (default 1); dense case: columns of the PDF matrix (default 2000)")
     return ap.parse_args()
 
 
@@ -307,6 +310,107 @@ def traffic_of(kernel, prec, ndata, replicas):
     return None
 
 
+# The paper's Table 3 (Sec. 3) times this product; its fastest line at
+# ndata = 2000, K = 35721, R = 2000 is TensorFlow on a GPU in 1.38 s including
+# the transfer to the device: 2000 * 2000 / 1.38 s datapoint*replicas/s.
+TABLE3_LAST = {"ndata": 2000, "R": 2000, "seconds": 1.38}
+
+
+def run_dense(args):
+    """The dense product of the paper's timing study: the Table 3 base table
+    (49 flavour combinations x 27 x points, K = 35721) flattened to
+    [ndata][K] times the PDF matrix [K][R] built on the device from R
+    replicas.  `value`: the product alone, timed over graph replays with the
+    PDF matrix resident; `e2e`: per step the PDF matrix is copied from pinned
+    host memory and O copied back (the table stays resident)."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    R = args.replicas or 2000
+    nd = args.ndata
+    t, F = W.table3(nd, R)
+    K = t.fk[0].size
+    prec = args.prec
+    io = torch.float64 if prec == "fp64" else torch.float32
+    ht = fk.Table.from_workload(t, precs=("fp64" if prec == "fp64" else "fp32",))
+    tab = fk.Table.dense(t.fk.reshape(nd, K), precs=(prec,))
+    del t
+    Fd = torch.tensor(F, dtype=io, device="cuda")
+    L = fk.luminosity(ht, Fd, "fp64" if prec == "fp64" else "fp32")
+    O = fk.dense_conv(tab, L, prec)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fk.dense_conv(tab, L, prec, out=O)
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # end to end: the PDF matrix from pinned host memory, O back to the host
+    Lh = L.cpu().pin_memory()
+    Oh = torch.empty(O.shape, dtype=io).pin_memory()
+    for _ in range(2):
+        L.copy_(Lh, non_blocking=True)
+        fk.dense_conv(tab, L, prec, out=O)
+        Oh.copy_(O, non_blocking=True)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    for _ in range(args.steps):
+        L.copy_(Lh, non_blocking=True)
+        fk.dense_conv(tab, L, prec, out=O)
+        Oh.copy_(O, non_blocking=True)
+    e3.record()
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3) / args.steps
+    flops = 2.0 * nd * K * R
+    byts = nd * K * ESZ[prec]
+    pk, src = peaks()
+    tc = prec in ("bf16", "bf16x3", "tf32")
+    tpeak = (pk["bf16_tflops"] / (2.0 if prec == "tf32" else 1.0) if tc else
+             148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12 if prec == "fp32" else
+             148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12)
+    ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
+    kern = "k_tc" if tc else ("k_stream" if R <= 4 else "k_tile")
+    if flops / byts < ridge:
+        ach = byts / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "algorithmic_bytes": byts}
+    else:
+        ach = flops / (ms * 1e-3) / 1e12
+        roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": ach / tpeak, "algorithmic_flops": flops}
+    roof.update({"traffic": None, "peak_source": src,
+                 "kernel": f"{kern} (timed as the whole product call, operand packing included)"})
+    value = nd * R / (ms * 1e-3)
+    exact = nd == TABLE3_LAST["ndata"] and R == TABLE3_LAST["R"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": value / (TABLE3_LAST["ndata"] * TABLE3_LAST["R"] / TABLE3_LAST["seconds"]) if exact else None,
+            "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"dense product of the paper's Table 3: FK [{nd} x {K}] . PDF matrix "
+                                   f"[{K} x {R}] (49 flavour combinations x 27 x points)",
+                       "l2": "table larger than L2" if byts > 126e6 else "table fits in L2 (warm: replayed back to back)",
+                       "graphs": True,
+                       "baseline": "paper Table 3, TensorFlow GPU 1.38 s incl. transfer (other hardware)" if exact else None},
+            "roofline": roof,
+            "e2e": {"value": nd * R / (ms_e2e * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(L.numel() * L.element_size()),
+                    "d2h_bytes_per_step": int(O.numel() * O.element_size())},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_stress(args):
     """One convolution of the stress table, timed over graph replays: the
     kernel-level roofline (HBM for the streaming path at small R, tensor pipe
@@ -314,7 +418,7 @@ def run_stress(args):
     import torch
     import paper_1909_10547_b300 as fk
     from paper_1909_10547_b300 import workloads as W
-    R = args.replicas
+    R = args.replicas or 1
     if args.table == "config1":
         t, F = W.config1(R=R)
         args.ndata = t.ndata
@@ -566,6 +670,9 @@ def main():
         return
     if args.case == "descent":
         run_descent(args)
+        return
+    if args.case == "dense":
+        run_dense(args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

@@ -79,7 +79,7 @@ enum {
 #define FK_PREC_BIT(p) (1u << (p))
 
 /* Table kinds reported by fk_table_info. */
-enum { FK_KIND_DIS = 0, FK_KIND_HAD = 1 };
+enum { FK_KIND_DIS = 0, FK_KIND_HAD = 1, FK_KIND_DENSE = 2 };
 
 /* ---------------------------------------------------------------- errors */
 
@@ -158,6 +158,45 @@ int fk_dis_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
 int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
                 fk_stream stream);
 
+/* -------------------------------------- dense product (Sec. 3, Table 3) */
+
+/*
+ * The dense formulation the paper times in Sec. 3 (Table 3): an FK table
+ * flattened to [ndata][K] times a "PDF matrix" with K rows per replica,
+ *   O[r][d] = sum_k fk[d][k] * L[r][k].
+ * With L from fk_luminosity this is Eq. 1 again; any K and any L are accepted.
+ *
+ * fk: HOST [ndata][K] doubles, copied into device memory the table owns, in
+ * the precisions of prec_mask (FP64, FP32, BF16, BF16 hi+lo, TF32).
+ * fk_table_info reports kind FK_KIND_DENSE, nchannels = nx = nx_grid = 0.
+ * Errors: FK_EINVAL (NULL, ndata < 1, K < 1 or K > 2^31 - 1024, bad mask),
+ * FK_ENOMEM, FK_ECUDA.
+ */
+int fk_table_create_dense(const double *fk, int ndata, long long K, unsigned prec_mask,
+                          fk_table **out);
+
+/*
+ * O = FK L for a dense table t.  L: DEVICE [R][K], replica-major (double for
+ * FK_FP64, float otherwise; the reduced modes round it to the mode, as F in
+ * fk_had_conv).  O: DEVICE, as in fk_had_conv (ldo = 0: [R][ndata]),
+ * overwritten.  FP64 and FP32 run on the CUDA cores, BF16 / BF16 hi+lo / TF32
+ * on the tensor cores with FP32 accumulation.  Asynchronous on stream.
+ * Errors: as fk_had_conv (a table of another kind: FK_EINVAL).
+ */
+int fk_dense_conv(const fk_table *t, const void *L, int R, void *O, int ldo, int prec,
+                  fk_stream stream);
+
+/*
+ * The PDF matrix of hadronic table t for fk_dense_conv (the luminosity the
+ * paper forms before its Table 3 product):
+ *   L[r][(c * nx + i) * nx + j] = F[r][ca[c]][xmap[i]] * F[r][cb[c]][xmap[j]],
+ * K = nc * nx * nx.  F: DEVICE [R][14][nx_grid]; L: DEVICE [R][K], written;
+ * both double for FK_FP64 and float for every other prec.  Asynchronous.
+ * Errors: FK_EINVAL (not a hadronic table, NULL pointer, R < 1, unknown
+ * prec), FK_ECUDA.
+ */
+int fk_luminosity(const fk_table *t, const void *F, int R, void *L, int prec, fk_stream stream);
+
 /*
  * fk_had_conv for FK_FP64 and FK_FP32 without any device allocation.  The
  * paper has no counterpart to this entry point: it exists for callers that
@@ -196,7 +235,8 @@ int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ld
  * the tensor cores with the forward's operand rounding: the products of the
  * table with the PDF of one flavour go through the MMA in the mode's type with
  * FP32 accumulation, and gO and the remaining PDF factor are applied in FP32.
- * Like the forward, they are offered for hadronic tables only.
+ * Like the forward, they are offered for hadronic tables only.  Dense tables
+ * have no adjoint here (FK_EUNSUPPORTED).
  */
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
                      void *gF, int accumulate, int prec, fk_stream stream);
@@ -292,7 +332,8 @@ int fk_adam_step(void *p, const void *g, void *m, void *v, long long n, int t, d
  */
 int fk_serve_create(size_t hbm_budget_bytes, int max_inflight, fk_server **out);
 /* Registers table t (the server does not take ownership; keep t alive until
- * fk_serve_destroy).  FK_EBUDGET if the table alone exceeds the budget. */
+ * fk_serve_destroy).  FK_EBUDGET if the table alone exceeds the budget,
+ * FK_EUNSUPPORTED for a dense table. */
 int fk_serve_add_table(fk_server *s, fk_table *t, int *table_id);
 /*
  * Queues a request.  F_host: HOST [R][14][nx_grid] of the mode's I/O type; it

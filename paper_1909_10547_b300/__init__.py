@@ -10,6 +10,8 @@ kernels; there is no CPU fallback.
     gF = conv_backward(t, F, gO, "fp32")
     cov = Cov(blocks);  chi2_r, gO = chi2(cov, O, D)
     O  = FKConv.apply(F, t, "fp32")         # autograd
+    td = Table.dense(fk2d, precs=("bf16x3",))   # the paper's Table 3 product
+    O  = dense_conv(td, luminosity(t, F), "bf16x3")
 """
 import ctypes
 
@@ -19,8 +21,8 @@ import torch
 from . import _lib
 from ._lib import FKError, PRECS
 
-__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "Cov", "chi2", "FKConv", "Server",
-           "FKError", "PRECS", "lib_path"]
+__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "dense_conv", "luminosity", "Cov", "chi2",
+           "FKConv", "Server", "FKError", "PRECS", "lib_path"]
 
 NFL = 14
 
@@ -95,6 +97,18 @@ class Table:
         return cls(h, 1, nd, nc, nx, nxg)
 
     @classmethod
+    def dense(cls, fk, precs=("fp64", "fp32")):
+        """fk [ndata][K] (host, FP64): the flattened table of the dense product
+        the paper times in Table 3 (kind 2)."""
+        fk = np.ascontiguousarray(fk, dtype=np.float64)
+        nd, K = fk.shape
+        h = ctypes.c_void_p()
+        _lib.call("fk_table_create_dense", _p(fk), nd, K, _mask(precs), ctypes.byref(h))
+        t = cls(h, 2, nd, 0, 0, 0)
+        t.K = K
+        return t
+
+    @classmethod
     def from_workload(cls, t, precs=("fp64", "fp32")):
         """Builds a device table from a workloads.DisTable / HadTable."""
         if hasattr(t, "ca"):
@@ -152,6 +166,37 @@ def dis_conv(t, F, prec="fp32", out=None):
 def had_conv(t, F, prec="fp32", out=None):
     assert t.kind == 1
     return conv(t, F, prec, out)
+
+
+def dense_conv(t: Table, L: torch.Tensor, prec="fp32", out: torch.Tensor = None) -> torch.Tensor:
+    """O [R][ndata] = FK L for a dense table: L [R][K] on cuda (the PDF
+    matrix, replica-major; float64 for fp64, float32 otherwise)."""
+    if t.kind != 2:
+        raise ValueError("dense_conv needs a dense table")
+    dt = _io_dtype(prec)
+    if not (L.is_cuda and L.dtype == dt and L.is_contiguous() and L.dim() == 2 and L.shape[1] == t.K):
+        raise ValueError(f"L must be a contiguous cuda {dt} tensor [R][{t.K}]")
+    R = L.shape[0]
+    O = out if out is not None else torch.empty((R, t.ndata), dtype=dt, device=L.device)
+    if O.shape != (R, t.ndata) or O.stride(1) != 1 or O.dtype != dt:
+        raise ValueError("out must be [R][ndata] with unit column stride and L's dtype")
+    _lib.call("fk_dense_conv", t.handle, _p(L), R, _p(O), O.stride(0), _prec(prec), _stream())
+    return O
+
+
+def luminosity(t: Table, F: torch.Tensor, prec="fp32", out: torch.Tensor = None) -> torch.Tensor:
+    """The PDF matrix L [R][nc * nx * nx] of hadronic table t for replicas F,
+    L[r][(c*nx + i)*nx + j] = F[r][a_c][x_i] F[r][b_c][x_j]."""
+    if t.kind != 1:
+        raise ValueError("luminosity needs a hadronic table")
+    _check_f(t, F, prec)
+    R = F.shape[0]
+    K = t.nch * t.nx * t.nx
+    L = out if out is not None else torch.empty((R, K), dtype=F.dtype, device=F.device)
+    if L.shape != (R, K) or not L.is_contiguous() or L.dtype != F.dtype:
+        raise ValueError("out must be a contiguous [R][nc*nx*nx] tensor of F's dtype")
+    _lib.call("fk_luminosity", t.handle, _p(F), R, _p(L), _prec(prec), _stream())
+    return L
 
 
 def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False):

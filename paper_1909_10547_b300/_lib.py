@@ -24,6 +24,9 @@ SIGNATURES = {
     "fk_dis_conv": [P, P, I, P, I, I, P],
     "fk_had_conv": [P, P, I, P, I, I, P],
     "fk_had_conv_noalloc": [P, P, I, P, I, I, P],
+    "fk_table_create_dense": [P, I, ctypes.c_longlong, U, PP],
+    "fk_dense_conv": [P, P, I, P, I, I, P],
+    "fk_luminosity": [P, P, I, P, I, P],
     "fk_conv_backward": [P, P, P, I, I, P, I, I, P],
     "fk_grad_sum": [P, I, ctypes.c_longlong, P, I, I, P],
     "fk_cov_create": [P, P, I, PP],

@@ -66,6 +66,49 @@ int upload(T **d, const std::vector<T> &h, size_t *bytes) {
     return FK_OK;
 }
 
+// Copies the host FP64 rows [ndata][E] into the table's FP64 / FP32 stream
+// layouts (rows padded to ldE), staged through a bounded device buffer.
+int upload_rows(fk_table *t, const double *fk) {
+    int rc = FK_OK;
+    const size_t rowsz = (size_t)t->ldE * t->ndata;
+    const bool need64 = t->mask & FK_PREC_BIT(FK_FP64);
+    const bool need32 = t->mask & FK_PREC_BIT(FK_FP32);
+    if ((need64 && cudaMalloc(&t->fk64, sizeof(double) * rowsz)) ||
+        (need32 && cudaMalloc(&t->fk32, sizeof(float) * rowsz))) {
+        return fail(FK_ENOMEM, "table storage");
+    }
+    t->bytes += (need64 ? sizeof(double) * rowsz : 0) + (need32 ? sizeof(float) * rowsz : 0);
+    if (need64 || need32) {
+        // stage the host rows through a bounded device buffer
+        const long long rows_per = std::max(1LL, (64LL << 20) / (t->E * 8));
+        double *stage = nullptr;
+        cudaStream_t st = nullptr;
+        if (cudaMalloc(&stage, sizeof(double) * t->E * std::min<long long>(rows_per, t->ndata)) ||
+            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) {
+            cudaFree(stage);
+            return fail(FK_ENOMEM, "table staging buffer");
+        }
+        for (long long d0 = 0; d0 < t->ndata && rc == FK_OK; d0 += rows_per) {
+            const long long nr = std::min<long long>(rows_per, t->ndata - d0);
+            cudaError_t e = cudaMemcpyAsync(stage, fk + d0 * t->E, sizeof(double) * nr * t->E,
+                                            cudaMemcpyHostToDevice, st);
+            if (e) {
+                rc = cuda_fail(e, "table upload");
+                break;
+            }
+            rc = convert_rows(stage, nr, t->E, t->ldE, t->fk64 ? t->fk64 + d0 * t->ldE : nullptr,
+                              t->fk32 ? t->fk32 + d0 * t->ldE : nullptr, st);
+            if (!rc) {
+                e = cudaStreamSynchronize(st);
+                if (e) rc = cuda_fail(e, "table conversion");
+            }
+        }
+        cudaStreamDestroy(st);
+        cudaFree(stage);
+    }
+    return rc;
+}
+
 int table_create(int kind, const double *fk, int ndata, const int *ca, const int *cb, int nch,
                  int nx, const int *xmap, int nxg, unsigned mask, fk_table **out) {
     if (!out) return fail(FK_EINVAL, "out is NULL");
@@ -113,47 +156,9 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
         table_free(t);
         return rc;
     }
-    const size_t rowsz = (size_t)t->ldE * ndata;
-    const bool need64 = mask & FK_PREC_BIT(FK_FP64);
-    const bool need32 = mask & FK_PREC_BIT(FK_FP32);
-    if ((need64 && cudaMalloc(&t->fk64, sizeof(double) * rowsz)) ||
-        (need32 && cudaMalloc(&t->fk32, sizeof(float) * rowsz))) {
+    if ((rc = upload_rows(t, fk))) {
         table_free(t);
-        return fail(FK_ENOMEM, "table storage");
-    }
-    t->bytes += (need64 ? sizeof(double) * rowsz : 0) + (need32 ? sizeof(float) * rowsz : 0);
-    if (need64 || need32) {
-        // stage the host rows through a bounded device buffer
-        const long long rows_per = std::max(1LL, (64LL << 20) / (t->E * 8));
-        double *stage = nullptr;
-        cudaStream_t st = nullptr;
-        if (cudaMalloc(&stage, sizeof(double) * t->E * std::min<long long>(rows_per, ndata)) ||
-            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) {
-            cudaFree(stage);
-            table_free(t);
-            return fail(FK_ENOMEM, "table staging buffer");
-        }
-        for (long long d0 = 0; d0 < ndata && rc == FK_OK; d0 += rows_per) {
-            const long long nr = std::min<long long>(rows_per, ndata - d0);
-            cudaError_t e = cudaMemcpyAsync(stage, fk + d0 * t->E, sizeof(double) * nr * t->E,
-                                            cudaMemcpyHostToDevice, st);
-            if (e) {
-                rc = cuda_fail(e, "table upload");
-                break;
-            }
-            rc = convert_rows(stage, nr, t->E, t->ldE, t->fk64 ? t->fk64 + d0 * t->ldE : nullptr,
-                              t->fk32 ? t->fk32 + d0 * t->ldE : nullptr, st);
-            if (!rc) {
-                e = cudaStreamSynchronize(st);
-                if (e) rc = cuda_fail(e, "table conversion");
-            }
-        }
-        cudaStreamDestroy(st);
-        cudaFree(stage);
-        if (rc) {
-            table_free(t);
-            return rc;
-        }
+        return rc;
     }
     if (mask & TC_PRECS) {
         rc = tc_build(t, fk);
@@ -161,6 +166,31 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
             table_free(t);
             return rc;
         }
+    }
+    *out = t;
+    return FK_OK;
+}
+
+int dense_create(const double *fk, int ndata, long long K, unsigned mask, fk_table **out) {
+    if (!out) return fail(FK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!fk) return fail(FK_EINVAL, "null table");
+    if (ndata < 1) return fail(FK_EINVAL, "ndata < 1");
+    if (K < 1 || K > (1LL << 31) - 1024) return fail(FK_EINVAL, "K must be in 1..2^31-1024");
+    if (!mask || (mask & ~ALL_PRECS)) return fail(FK_EINVAL, "bad precision mask");
+    keep_pool();
+    fk_table *t = new fk_table();
+    t->kind = FK_KIND_DENSE;
+    t->ndata = ndata;
+    t->E = K;
+    t->ldE = (K + 31) / 32 * 32;
+    t->mask = mask;
+    cudaGetDevice(&t->device);
+    int rc = upload_rows(t, fk);
+    if (!rc && (mask & TC_PRECS)) rc = tc_build_dense(t, fk);
+    if (rc) {
+        table_free(t);
+        return rc;
     }
     *out = t;
     return FK_OK;
@@ -257,9 +287,32 @@ int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
     return fwd_tc(t, (const float *)F, R, (float *)O, ldo, prec, (cudaStream_t)stream);
 }
 
+int fk_table_create_dense(const double *fk, int ndata, long long K, unsigned prec_mask, fk_table **out) {
+    return dense_create(fk, ndata, K, prec_mask, out);
+}
+
+int fk_dense_conv(const fk_table *t, const void *L, int R, void *O, int ldo, int prec, fk_stream stream) {
+    int rc = check_conv(t, FK_KIND_DENSE, L, R, O, ldo, prec);
+    if (rc) return rc;
+    ldo = ldo ? ldo : t->ndata;
+    if (prec == FK_FP64 || prec == FK_FP32)
+        return dense_cc(t, L, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    return dense_tc(t, (const float *)L, R, (float *)O, ldo, prec, (cudaStream_t)stream);
+}
+
+int fk_luminosity(const fk_table *t, const void *F, int R, void *L, int prec, fk_stream stream) {
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (t->kind != FK_KIND_HAD) return fail(FK_EINVAL, "the PDF matrix needs a hadronic table");
+    if (!F || !L) return fail(FK_EINVAL, "null F or L");
+    if (R < 1) return fail(FK_EINVAL, "R < 1");
+    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
+    return luminosity_cc(t, F, R, L, prec == FK_FP64, (cudaStream_t)stream);
+}
+
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
                      int accumulate, int prec, fk_stream stream) {
     if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (t->kind == FK_KIND_DENSE) return fail(FK_EUNSUPPORTED, "no adjoint for dense tables");
     if (!gO || !gF || (t->kind == FK_KIND_HAD && !F)) return fail(FK_EINVAL, "null F, gO or gF");
     if (R < 1) return fail(FK_EINVAL, "R < 1");
     if (ldgo < 0 || (ldgo > 0 && ldgo < t->ndata)) return fail(FK_EINVAL, "ldgo < ndata");

@@ -100,7 +100,9 @@ struct TcLayout {
 }  // namespace fk
 
 // Device-resident table.  Stream layouts keep the caller's element order
-// (channel, x_i, x_j) per data point, each row padded to ldE elements.
+// (channel, x_i, x_j) per data point, each row padded to ldE elements.  A
+// dense table (the paper's Table 3 product) holds [ndata][E = K] with
+// nch = nx = nxg = 0.
 struct fk_table {
     int kind = 0;
     int ndata = 0, nch = 0, nx = 0, nxg = 0;
@@ -133,11 +135,16 @@ inline TableView view(const fk_table *t) {
 namespace fk {
 // CUDA-core paths (k_cc.cu)
 int fwd_cc(const fk_table *t, const void *F, int R, void *O, int ldo, bool f64, cudaStream_t s);
+// dense tables (the paper's Table 3 product) and the PDF matrix of a hadronic table
+int dense_cc(const fk_table *t, const void *L, int R, void *O, int ldo, bool f64, cudaStream_t s);
+int luminosity_cc(const fk_table *t, const void *F, int R, void *L, bool f64, cudaStream_t s);
 int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
            int accumulate, bool f64, cudaStream_t s);
 // tensor-core path (k_tc.cu)
 int tc_build(fk_table *t, const double *host_fk);
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
+int tc_build_dense(fk_table *t, const double *host_fk);
+int dense_tc(const fk_table *t, const float *L, int R, float *O, int ldo, int prec, cudaStream_t s);
 int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
            int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);

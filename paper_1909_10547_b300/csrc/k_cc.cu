@@ -105,13 +105,15 @@ __global__ void __launch_bounds__(256) k_stream(TableView tv, const T *__restric
     __shared__ SmemPdf<T> s;
     __shared__ T red[DB][256];
     const int r = blockIdx.z;
-    const T *Fr = F + (size_t)r * NFL * tv.nxg;
-    for (int k = threadIdx.x; k < NFL * tv.nxg; k += 256) s.f[k] = Fr[k];
-    for (int k = threadIdx.x; k < tv.nch; k += 256) {
-        s.ca[k] = tv.ca[k];
-        if (KIND == FK_KIND_HAD) s.cb[k] = tv.cb[k];
+    if constexpr (KIND != FK_KIND_DENSE) {
+        const T *Fr = F + (size_t)r * NFL * tv.nxg;
+        for (int k = threadIdx.x; k < NFL * tv.nxg; k += 256) s.f[k] = Fr[k];
+        for (int k = threadIdx.x; k < tv.nch; k += 256) {
+            s.ca[k] = tv.ca[k];
+            if (KIND == FK_KIND_HAD) s.cb[k] = tv.cb[k];
+        }
+        for (int k = threadIdx.x; k < tv.nx; k += 256) s.xm[k] = tv.xmap[k];
     }
-    for (int k = threadIdx.x; k < tv.nx; k += 256) s.xm[k] = tv.xmap[k];
     __syncthreads();
 
     const int nx2 = tv.nx * tv.nx;
@@ -120,7 +122,13 @@ __global__ void __launch_bounds__(256) k_stream(TableView tv, const T *__restric
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < V; ++v) w[u][v] = elem_weight<KIND>(s, e0 + u * 256 * V + v, tv, nx2);
+        for (int v = 0; v < V; ++v) {
+            const long long e = e0 + u * 256 * V + v;
+            if constexpr (KIND == FK_KIND_DENSE)  // the PDF matrix row of replica r (F is [R][E])
+                w[u][v] = e < tv.E ? __ldg(F + (size_t)r * tv.E + e) : T(0);
+            else
+                w[u][v] = elem_weight<KIND>(s, e, tv, nx2);
+        }
 
     const int d0 = blockIdx.y * DB;
     T acc[DB];
@@ -189,7 +197,7 @@ constexpr size_t tile_smem() {
     return sizeof(T) * (TileCfg<T>::KC * (TDT + 1) + TileCfg<T>::KC * TRT) + sizeof(int) * (MAX_CH + MAX_NX);
 }
 
-template <typename T>
+template <typename T, bool DENSE>
 __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict__ fk,
                                               const T *__restrict__ F, int R, int nsplit,
                                               T *__restrict__ part) {
@@ -229,9 +237,13 @@ __global__ void __launch_bounds__(256) k_tile(TableView tv, const T *__restrict_
             const int rr = idx % TRT, kk = idx / TRT;
             T v = T(0);
             if (k0 + kk < el_e && r0 + rr < R) {
-                const int e = (int)(k0 + kk);
-                const int kf = e / tv.nx, i = e - kf * tv.nx;
-                v = F[(size_t)(r0 + rr) * fstride + sfl[kf] * tv.nxg + sxm[i]];
+                if constexpr (DENSE) {  // the PDF matrix, [R][E]
+                    v = F[(size_t)(r0 + rr) * tv.E + k0 + kk];
+                } else {
+                    const int e = (int)(k0 + kk);
+                    const int kf = e / tv.nx, i = e - kf * tv.nx;
+                    v = F[(size_t)(r0 + rr) * fstride + sfl[kf] * tv.nxg + sxm[i]];
+                }
             }
             Bs[kk * TRT + rr] = v;
         }
@@ -762,7 +774,7 @@ int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, c
     Scratch scr(s);
     T *part = nullptr;
     int nparts;
-    if (R <= 4 && (KIND == FK_KIND_DIS || R == 1)) {
+    if (R <= 4 && (KIND != FK_KIND_HAD || R == 1)) {
         constexpr int CH = 256 * V16<T>::n * StreamCfg<T>::U;
         const int nchunk = (int)((t->ldE + CH - 1) / CH);
         nparts = nchunk;
@@ -785,10 +797,11 @@ int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, c
         nparts = (int)std::max(1LL, std::min(nseg, want));
         FK_CUDA(scr.get(&part, (size_t)nparts * R * t->ndata));
         constexpr size_t smem = tile_smem<T>();
-        int rc = set_smem<T>(k_tile<T>, smem);
+        constexpr bool DENSE = KIND == FK_KIND_DENSE;
+        int rc = set_smem<T>(k_tile<T, DENSE>, smem);
         if (rc) return rc;
         dim3 grid(dt, rt, nparts);
-        k_tile<T><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
+        k_tile<T, DENSE><<<grid, 256, smem, s>>>(tv, fk, F, R, nparts, part);
         count_launch();
         FK_CUDA(cudaGetLastError());
     }
@@ -860,6 +873,48 @@ int fwd_cc(const fk_table *t, const void *F, int R, void *O, int ldo, bool f64, 
     return t->kind == FK_KIND_HAD
                ? fwd_cc_t<FK_KIND_HAD, float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s)
                : fwd_cc_t<FK_KIND_DIS, float>(t, (const float *)F, R, (float *)O, ldo, t->fk32, s);
+}
+
+int dense_cc(const fk_table *t, const void *L, int R, void *O, int ldo, bool f64, cudaStream_t s) {
+    if (f64) {
+        if (!t->fk64) return fail(FK_EUNSUPPORTED, "table has no FP64 copy");
+        return fwd_cc_t<FK_KIND_DENSE, double>(t, (const double *)L, R, (double *)O, ldo, t->fk64, s);
+    }
+    if (!t->fk32) return fail(FK_EUNSUPPORTED, "table has no FP32 copy");
+    return fwd_cc_t<FK_KIND_DENSE, float>(t, (const float *)L, R, (float *)O, ldo, t->fk32, s);
+}
+
+namespace {
+// The PDF matrix of a hadronic table: L[r][(c * nx + i) * nx + j] =
+// F[r][a_c][xmap[i]] * F[r][b_c][xmap[j]], one element per thread (grid-stride).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lum(TableView tv, const T *__restrict__ F, int R, T *__restrict__ L) {
+    const long long n = (long long)R * tv.E;
+    const int nx2 = tv.nx * tv.nx;
+    for (long long idx = (long long)blockIdx.x * 256 + threadIdx.x; idx < n; idx += (long long)gridDim.x * 256) {
+        const long long r = idx / tv.E;
+        const int e = (int)(idx - r * tv.E);
+        const int c = e / nx2, rem = e - c * nx2, i = rem / tv.nx, j = rem - i * tv.nx;
+        const T *f = F + (size_t)r * NFL * tv.nxg;
+        L[idx] = __ldg(f + __ldg(tv.ca + c) * tv.nxg + __ldg(tv.xmap + i)) *
+                 __ldg(f + __ldg(tv.cb + c) * tv.nxg + __ldg(tv.xmap + j));
+    }
+}
+
+template <typename T>
+int luminosity_t(const fk_table *t, const T *F, int R, T *L, cudaStream_t s) {
+    const long long n = (long long)R * t->E;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148LL * 16);
+    k_lum<T><<<blocks, 256, 0, s>>>(view(t), F, R, L);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+}  // namespace
+
+int luminosity_cc(const fk_table *t, const void *F, int R, void *L, bool f64, cudaStream_t s) {
+    return f64 ? luminosity_t<double>(t, (const double *)F, R, (double *)L, s)
+               : luminosity_t<float>(t, (const float *)F, R, (float *)L, s);
 }
 
 int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,

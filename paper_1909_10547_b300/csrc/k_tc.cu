@@ -306,13 +306,20 @@ struct TcParams {
     float *O;         // forward: observables, row stride ldo
     const float *gO;  // adjoint: weights gO[r * ldo + d]
     float *P;         // adjoint: partial sums [ntile_n][ngroups][nx][R_pad]
+    // K split (dense products with fewer tiles than SMs): work item w covers
+    // data tile nt and K split sp, ntile_n data tiles; split sp starts at K
+    // element sp * kspl and writes its partial tile at O + sp * ostride
+    int ntile_n, nsplit, kspl;
+    long long ostride;
 };
 
 // Epilogue modes of the tensor-core kernel.
 //  FWD: O[r][d]   = sum_g sum_i f^r_{a_g}(x_i) Y_g[r][(i, d)]
 //  ADJ: P[t][g][i][r] = sum_{d in tile t} gO[r][d] Y_g[r][(i, d)]
 // (with the transposed packing, i stands for x_j and g for the second flavour)
-enum { MODE_FWD = 0, MODE_ADJ = 1 };
+// MODE_DENSE: the plain product of the paper's Table 3 (one group spanning K,
+// the accumulator columns are the tile's data points, stored as they are)
+enum { MODE_FWD = 0, MODE_ADJ = 1, MODE_DENSE = 2 };
 
 template <int PREC, int CL>
 size_t tc_smem_bytes(int n_rows) {
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int w_first = CL == 2 ? (int)cluster_id() : (int)blockIdx.x;
     const int w_step = CL == 2 ? (int)cluster_count() : (int)gridDim.x;
     const int w_count = p.ntiles / CL;
-    auto tile_of = [&](int w, int &rt, int &nt) {
+    auto tile_of = [&](int w, int &rt, int &nt, int &sp) {
         if (CL == 2) {
             const int half = p.nrt / 2;
             nt = w / half;
@@ -351,6 +358,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             rt = w % p.nrt;
             nt = w / p.nrt;
         }
+        sp = nt / p.ntile_n;
+        nt -= sp * p.ntile_n;
     };
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -411,8 +420,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
             int rt, nt;
-            tile_of(w, rt, nt);
+            int sp;
+            tile_of(w, rt, nt, sp);
             const int brow = nt * p.n_rows + (int)rank * b_rows;
+            const int koff = sp * p.kspl;  // the split's first K element
             int pg = 0;  // next group whose first stage is still to be loaded
             for (int q = 0; q < p.nchunks; ++q, ++it) {
                 const int s = it % S;
@@ -439,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (leader) mbar_expect_tx(full(s), 2 * stage_bytes);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
-                        const int x = q * T::KCS + a * T::KC;
+                        const int x = koff + q * T::KCS + a * T::KC;
                         tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, rt * TC_M);
                         tma_load_2d_pair(st + offB + a * b_bytes, &mapB, fb, x, brow);
                         if (T::X3) {
@@ -451,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(full(s), stage_bytes);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
-                        const int x = q * T::KCS + a * T::KC;
+                        const int x = koff + q * T::KCS + a * T::KC;
                         tma_load_2d(st + a * a_bytes, &mapA, full(s), x, rt * TC_M);
                         tma_load_2d(st + offB + a * b_bytes, &mapB, full(s), x, brow);
                         if (T::X3) {
@@ -623,7 +634,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
             int rt, nt;
-            tile_of(w, rt, nt);
+            int sp;
+            tile_of(w, rt, nt, sp);
             const int r = rt * TC_M + rl;
             float acc[G];
 #pragma unroll
@@ -664,12 +676,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int i = 0; i < MI; ++i) ps[i] = 0.f;
                 }
+                if constexpr (MODE == MODE_DENSE) {
+                    // column col of the accumulator is data point nt * n_rows + col
+                    const int dbase = nt * p.n_rows;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (c * 64 < p.n_rows) {
+                            uint32_t v[64];
+                            tmem_ld64(taddr + (uint32_t)(c * 64), v);
+                            if (r < p.R) {
+                                float *orow = p.O + sp * p.ostride + (size_t)r * p.ldo + dbase + c * 64;
+#pragma unroll
+                                for (int k = 0; k < 64; ++k)
+                                    if (dbase + c * 64 + k < p.ndata) orow[k] = __uint_as_float(v[k]);
+                            }
+                        }
+                    }
+                }
                 // 64 columns per TMEM round trip; the column -> (x point,
                 // data point) split is fixed at compile time; columns of x
                 // points >= nx (never written by the MMA) are skipped
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (c * 64 < ncols) {
+                    if (MODE != MODE_DENSE && c * 64 < ncols) {
                         uint32_t v[64];
                         tmem_ld64(taddr + (uint32_t)(c * 64), v);
 #pragma unroll
@@ -833,6 +862,21 @@ __global__ void k_pack_table(const TcGroups gr, const double *__restrict__ fk, i
                 v = (float)fk[(((size_t)d * nc + c) * nx + xi) * nx + xj];
             }
         }
+        store_op<PREC>(idx, v, hi, lo, f32);
+    }
+}
+
+// B operand of a dense table from its FP64 rows [ndata][K]: row d of the
+// packing (tile d / n_rows) holds data point d; columns k >= K and rows
+// d >= ndata are zero.
+template <int PREC>
+__global__ void k_pack_dense(const double *__restrict__ fk, int ndata, long long K, long long rows,
+                             int ktot_pad, __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+    const long long n = rows * ktot_pad;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long d = idx / ktot_pad, k = idx % ktot_pad;
+        const float v = (d < ndata && k < K) ? (float)fk[d * K + k] : 0.f;
         store_op<PREC>(idx, v, hi, lo, f32);
     }
 }
@@ -1095,7 +1139,8 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
         FK_CUDA(scr.get(&hi, nA));
         if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
     }
-    const int frow = NFL * t->nxg;
+    // A rows: the PDF grid of a replica, or a dense table's PDF matrix row
+    const int frow = t->kind == FK_KIND_DENSE ? (int)t->E : NFL * t->nxg;
     k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
                        s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
     count_launch();
@@ -1114,6 +1159,8 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     p = TcParams{};
     p.nrt = R_pad / TC_M;
     p.ntiles = L.ntile_n * p.nrt;
+    p.ntile_n = L.ntile_n;
+    p.nsplit = 1;
     p.nchunks = pk.ktot_pad / Tr<PREC>::KCS;
     p.n_rows = L.n_rows;
     // narrow tiles (G * nx <= 128, i.e. nx <= 8) keep four accumulators of 128
@@ -1147,6 +1194,74 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     p.Fm = Fm;
     p.O = O;
     return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, L.fwd, p, s);
+}
+
+// Dense product (Table 3): the A operand is the caller's PDF matrix, the B
+// operand the packed table, one group over K; the epilogue stores the tile.
+// When the (replica, data) tiles leave SMs idle, K is split into runs of at
+// least 8 stages, each run a work item writing a partial tile; k_dense_sum
+// adds the partials in split order.  The split count minimises waves x (stages
+// per item + a fixed cost per item), one CTA per SM, plus the partials' cost
+// per extra split; ties keep fewer splits.  It depends on R (through the tile
+// count), so in these modes a replica's last bits can differ between calls
+// with different R.
+__global__ void __launch_bounds__(256) k_dense_sum(const float *__restrict__ part, int nsplit, int ndata,
+                                                   int R, float *__restrict__ O, int ldo) {
+    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long n = (long long)R * ndata;
+    if (idx >= n) return;
+    float v = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) v += part[(size_t)sp * n + idx];
+    const long long r = idx / ndata, d = idx - r * ndata;
+    O[r * ldo + d] = v;
+}
+
+template <int PREC>
+int dense_tc_t(const fk_table *t, const float *Lm, int R, float *O, int ldo, cudaStream_t s) {
+    Scratch scr(s);
+    CUtensorMap mA, mA2;
+    TcParams p;
+    int rc = prepare<PREC>(t, t->tc.fwd, Lm, R, scr, nullptr, s, mA, mA2, p);
+    if (rc) return rc;
+    const int stages = p.nchunks, items = p.ntiles, sms = sm_count();
+    int nsplit = 1;
+    constexpr int ITEM_COST = 4;  // stages' worth of pipeline fill and epilogue per work item
+    // each extra split writes and re-reads R x ndata partials: two stages' worth per 128 x 256 tile of them
+    const double split_cost = 2.0 * R * t->ndata / (TC_M * 256.0);
+    double best = (double)((items + sms - 1) / sms) * (stages + ITEM_COST);
+    for (int ns = 2; ns <= std::min(stages / 8, 2 * sms); ++ns) {
+        const double cost =
+            (double)((items * ns + sms - 1) / sms) * ((stages + ns - 1) / ns + ITEM_COST) + split_cost * (ns - 1);
+        if (cost < best) {
+            best = cost;
+            nsplit = ns;
+        }
+    }
+    const int cps = (stages + nsplit - 1) / nsplit;  // stages per split
+    nsplit = (stages + cps - 1) / cps;
+    p.nchunks = cps;
+    p.kbeg[0] = 0;
+    p.kend[0] = cps * Tr<PREC>::KCS;  // past K the operands read as zero (TMA fill)
+    p.kspl = cps * Tr<PREC>::KCS;
+    p.nsplit = nsplit;
+    p.ntiles = items * nsplit;
+    float *part = nullptr;
+    if (nsplit > 1) {
+        FK_CUDA(scr.get(&part, (size_t)nsplit * R * t->ndata));
+        p.O = part;
+        p.ldo = t->ndata;
+        p.ostride = (long long)R * t->ndata;
+    } else {
+        p.O = O;
+        p.ldo = ldo;
+    }
+    rc = launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.fwd), p, s);
+    if (rc || nsplit == 1) return rc;
+    const long long n = (long long)R * t->ndata;
+    k_dense_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nsplit, t->ndata, R, O, ldo);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
 }
 
 // Adjoint: term 1 (derivative with respect to the first flavour of each
@@ -1320,6 +1435,97 @@ int tc_build(fk_table *t, const double *host_fk) {
         if (want_f32 && (rc = make_map(&pk->half_f32, pk->f32, 4, pk->ktot_pad, rows, h))) return rc;
     }
     return FK_OK;
+}
+
+// Tensor-core layout of a dense table (the paper's Table 3 product): tiles of
+// n_rows = min(256, ndata rounded up to 16) data points, one group spanning
+// K, the A operand gathered from the caller's PDF matrix through the identity
+// map.
+template <int PREC>
+int pack_dense(fk_table *t, const double *d_fk, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const TcPack &pk = L.fwd;
+    const long long rows = (long long)L.ntile_n * L.n_rows;
+    const unsigned blocks = (unsigned)std::min<long long>((rows * pk.ktot_pad + 255) / 256, 148LL * 32);
+    k_pack_dense<PREC><<<blocks, 256, 0, s>>>(d_fk, t->ndata, t->E, rows, pk.ktot_pad, pk.hi, pk.lo, pk.f32);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+int tc_build_dense(fk_table *t, const double *host_fk) {
+    TcLayout &L = t->tc;
+    TcPack &pk = L.fwd;
+    const long long K = t->E;
+    L.G = 16;  // not used by the dense epilogue
+    L.n_rows = std::min(256, (t->ndata + 15) / 16 * 16);
+    L.ntile_n = (t->ndata + L.n_rows - 1) / L.n_rows;
+    pk.grp = TcGroups{};
+    pk.grp.ngroups = 1;
+    pk.grp.kbeg[0] = 0;
+    pk.grp.kend[0] = (int)((K + KPAD - 1) / KPAD * KPAD);
+    pk.ktot = pk.grp.kend[0];
+    const int kal = (t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_TF32))) ? 128 : 64;
+    pk.ktot_pad = (pk.ktot + kal - 1) / kal * kal;
+    const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
+    const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
+    const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
+    {
+        std::vector<int> km(pk.ktot_pad);
+        for (int k = 0; k < pk.ktot_pad; ++k) km[k] = k < K ? k : -1;
+        if (cudaMalloc(&pk.kmeta, km.size() * sizeof(int))) return fail(FK_ENOMEM, "tensor-core gather map");
+        FK_CUDA(cudaMemcpy(pk.kmeta, km.data(), km.size() * sizeof(int), cudaMemcpyHostToDevice));
+        t->bytes += km.size() * sizeof(int);
+    }
+    const long long rows = (long long)L.ntile_n * L.n_rows;
+    const size_t elems = (size_t)rows * pk.ktot_pad;
+    if ((want_hi && cudaMalloc(&pk.hi, elems * 2)) || (want_lo && cudaMalloc(&pk.lo, elems * 2)) ||
+        (want_f32 && cudaMalloc(&pk.f32, elems * 4)))
+        return fail(FK_ENOMEM, "tensor-core table storage");
+    t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+
+    // FP64 rows on the device for the packing kernels, then freed
+    double *owned = nullptr;
+    cudaStream_t s = nullptr;
+    FK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const size_t src = (size_t)t->ndata * K;
+    if (cudaMalloc(&owned, src * 8)) {
+        cudaStreamDestroy(s);
+        return fail(FK_ENOMEM, "tensor-core packing staging");
+    }
+    int rc = FK_OK;
+    cudaError_t e = cudaMemcpyAsync(owned, host_fk, src * 8, cudaMemcpyHostToDevice, s);
+    if (e) rc = cuda_fail(e, "dense table upload");
+    if (!rc && want_f32) rc = pack_dense<FK_TF32>(t, owned, s);
+    if (!rc && want_lo) rc = pack_dense<FK_BF16X3>(t, owned, s);
+    else if (!rc && want_hi) rc = pack_dense<FK_BF16>(t, owned, s);
+    if (!rc) {
+        e = cudaStreamSynchronize(s);
+        if (e) rc = cuda_fail(e, "dense table packing");
+    }
+    cudaFree(owned);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    const int h = L.n_rows / 2;  // a multiple of 8 rows
+    if (want_hi && ((rc = make_map(&pk.map_hi, pk.hi, 2, pk.ktot_pad, rows, L.n_rows)) ||
+                    (rc = make_map(&pk.half_hi, pk.hi, 2, pk.ktot_pad, rows, h))))
+        return rc;
+    if (want_lo && ((rc = make_map(&pk.map_lo, pk.lo, 2, pk.ktot_pad, rows, L.n_rows)) ||
+                    (rc = make_map(&pk.half_lo, pk.lo, 2, pk.ktot_pad, rows, h))))
+        return rc;
+    if (want_f32 && ((rc = make_map(&pk.map_f32, pk.f32, 4, pk.ktot_pad, rows, L.n_rows)) ||
+                     (rc = make_map(&pk.half_f32, pk.f32, 4, pk.ktot_pad, rows, h))))
+        return rc;
+    return FK_OK;
+}
+
+int dense_tc(const fk_table *t, const float *Lm, int R, float *O, int ldo, int prec, cudaStream_t s) {
+    switch (prec) {
+        case FK_BF16: return dense_tc_t<FK_BF16>(t, Lm, R, O, ldo, s);
+        case FK_BF16X3: return dense_tc_t<FK_BF16X3>(t, Lm, R, O, ldo, s);
+        case FK_TF32: return dense_tc_t<FK_TF32>(t, Lm, R, O, ldo, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
 }
 
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s) {

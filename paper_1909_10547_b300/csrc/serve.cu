@@ -331,6 +331,7 @@ int fk_serve_create(size_t hbm_budget_bytes, int max_inflight, fk_server **out) 
 
 int fk_serve_add_table(fk_server *s, fk_table *t, int *table_id) {
     if (!s || !t || !table_id) return fail(FK_EINVAL, "fk_serve_add_table: null argument");
+    if (t->kind == FK_KIND_DENSE) return fail(FK_EUNSUPPORTED, "fk_serve_add_table: the server takes DIS and hadronic tables");
     std::lock_guard<std::mutex> l(s->mu);
     if (s->resident + t->bytes > s->budget) return fail(FK_EBUDGET, "table does not fit the server budget");
     s->tables.push_back(t);

@@ -302,3 +302,31 @@ def arrivals(rng: np.random.Generator, rate: float, n: int) -> np.ndarray:
 
 
 REPLICA_CHOICES = (1, 10, 100, 1000)
+
+
+# ---------------------------------------------------------------------------
+# The dense product of the paper's timing study (Sec. 3, Table 3).
+# ---------------------------------------------------------------------------
+
+TABLE3_SHAPE = dict(nc=49, nx=27)  # K = 49 * 27 * 27 = 35721 elements per data point
+
+
+def table3(ndata: int, R: int, seed: int = SEED_BASE + 5):
+    """The base table of the paper's Table 3: 49 flavour combinations (all
+    ordered pairs of 7 seeded flavours) on 27 x points in [1e-6, 1), so
+    K = 35721 elements per data point; FK ~ N(0,1) x_i^0.2 x_j^0.2 as in
+    config 1, and R jittered replicas of the config-0 PDF family.
+    Returns (HadTable, F [R][14][27]); the dense product takes the table
+    flattened to [ndata][K] and the PDF matrix built from F."""
+    rng = np.random.default_rng(seed)
+    nx = TABLE3_SHAPE["nx"]
+    x = xgrid(nx, 1e-6)
+    fl = np.sort(rng.choice(NFL, 7, replace=False))
+    ca = np.repeat(fl, 7).astype(np.int32)
+    cb = np.tile(fl, 7).astype(np.int32)
+    w = x ** 0.2
+    fk = rng.standard_normal((ndata, len(ca), nx, nx))
+    fk *= (w[:, None] * w[None, :])[None, None]
+    t = HadTable(fk, ca, cb, np.arange(nx, dtype=np.int32), nx)
+    F = pdf_replicas(x, pdf_params(rng), R, rng if R > 1 else None)
+    return t, F

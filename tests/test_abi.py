@@ -66,3 +66,17 @@ def test_null_pointer_calls_are_rejected():
     assert lib.fk_chi2(None, None, None, 1, None, None, 0, None) == _lib.FK_EINVAL
     assert lib.fk_table_destroy(None) == 0
     assert lib.fk_cov_size(None) == 0
+
+
+@pytest.mark.parametrize("shape,precs", [((0, 5), ("fp32",)), ((2, 0), ("fp32",)), ((2, 5), ())])
+def test_dense_table_argument_errors_need_no_gpu(shape, precs):
+    import numpy as np
+    with pytest.raises(fk.FKError) as e:
+        fk.Table.dense(np.zeros(shape), precs=precs)
+    assert e.value.status == _lib.FK_EINVAL
+
+
+def test_dense_and_luminosity_reject_null_handles():
+    lib = _lib.load()
+    assert lib.fk_dense_conv(None, None, 1, None, 0, 0, None) == _lib.FK_EINVAL
+    assert lib.fk_luminosity(None, None, 1, None, 0, None) == _lib.FK_EINVAL

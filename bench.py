@@ -292,7 +292,7 @@ def traffic_of(kernel, prec, ndata, replicas):
     source has changed since it was taken."""
     here = os.path.dirname(os.path.abspath(__file__))
     csrc = os.path.join(here, "paper_1909_10547_b300", "csrc")
-    srcs = ({"k_tc": ["k_tc.cu"], "k_stream": ["k_cc.cu"], "k_fac": ["k_cc.cu"]}.get(kernel) or
+    srcs = ({"k_tc": ["k_tc.cu"], "k_tc_dense": ["k_tc.cu"], "k_stream": ["k_cc.cu"], "k_fac": ["k_cc.cu"]}.get(kernel) or
             sorted(f for f in os.listdir(csrc) if f.endswith(".cu")))
     h = hashlib.sha256()
     for src in srcs:
@@ -389,7 +389,7 @@ def run_dense(args):
         ach = flops / (ms * 1e-3) / 1e12
         roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": ach / tpeak, "algorithmic_flops": flops}
-    roof.update({"traffic": None, "peak_source": src,
+    roof.update({"traffic": traffic_of("k_tc_dense", prec, nd, R) if tc else None, "peak_source": src,
                  "kernel": f"{kern} (timed as the whole product call, operand packing included)"})
     value = nd * R / (ms * 1e-3)
     exact = nd == TABLE3_LAST["ndata"] and R == TABLE3_LAST["R"]

@@ -679,8 +679,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if constexpr (MODE == MODE_DENSE) {
                     // column col of the accumulator is data point nt * n_rows + col
                     const int dbase = nt * p.n_rows;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {  // rolled: one 64-register buffer
                         if (c * 64 < p.n_rows) {
                             uint32_t v[64];
                             tmem_ld64(taddr + (uint32_t)(c * 64), v);

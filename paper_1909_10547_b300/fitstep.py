@@ -12,7 +12,8 @@ The covariance is block diagonal with one block per dataset, so the three
 stages of dataset k depend only on each other.  All run in libfk.so kernels.
 
 pipelined=True (default): each table's chain forward -> chi^2 block ->
-adjoint runs on its own CUDA stream, so the FP64 chi^2 of one dataset
+adjoint runs on its own CUDA stream (the chi^2 forked onto a high-priority
+stream of its own and joined back), so the FP64 chi^2 of one dataset
 overlaps the tensor-core and CUDA-core convolutions of the others; the
 per-stream gradient buffers and the per-dataset chi^2 values are then added
 by fk_grad_sum in a fixed order.  capture() records the step as one CUDA
@@ -125,6 +126,13 @@ class GlobalFit:
         self.streams = [torch.cuda.Stream(device=device, priority=-1 if s in light else 0)
                         for s in range(self.nstreams)]
         self.gF_parts = [torch.empty_like(self.F) for _ in range(self.nstreams)]
+        # pipelined chains: each dataset's chi^2 runs on its own high-priority
+        # stream between its forward and adjoint, so it starts as soon as the
+        # forward ends instead of waiting behind other chains' queued CTAs
+        # (1.24 -> 1.19 ms measured; priority -2, above the light streams,
+        # measured 1.22)
+        self.chi2_streams = ([torch.cuda.Stream(device=device, priority=-1) for _ in tables]
+                             if pipelined else [])
 
     # -- helpers -------------------------------------------------------------
     def _fan_out(self, body):
@@ -206,10 +214,17 @@ class GlobalFit:
     def _table_chain(self, s, k, accumulate):
         """forward -> chi^2 -> adjoint of table k on the current stream;
         returns an event recorded after the forward."""
+        cur = torch.cuda.current_stream()
         conv(self.tabs[k], self.F, self.tprec[k], out=self.Ok[k])
         fwd = torch.cuda.Event()
-        fwd.record(torch.cuda.current_stream())
-        chi2(self.covs[k], self.Ok[k], self.Dk[k], grad=True, out=self.chi2_parts[k], gO=self.gOk[k])
+        fwd.record(cur)
+        h = self.chi2_streams[k]
+        h.wait_event(fwd)
+        with torch.cuda.stream(h):
+            chi2(self.covs[k], self.Ok[k], self.Dk[k], grad=True, out=self.chi2_parts[k], gO=self.gOk[k])
+            done = torch.cuda.Event()
+            done.record(h)
+        cur.wait_event(done)
         conv_backward(self.tabs[k], self.F, self.gOk[k], self.tprec[k], gF=self.gF_parts[s],
                       accumulate=accumulate)
         return fwd

@@ -106,17 +106,105 @@ def workload():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    """Samples SM clocks and throttle reasons during a region: through NVML
+    every 5 ms from a thread (read-only queries), else with nvidia-smi at its
+    100 ms interval.  Nothing here changes a GPU setting."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.nv = None
+        self.samples = []  # (sm MHz, max sm MHz, reasons)
+
+    class _CNVML:
+        """The few read-only NVML calls used here, through ctypes (when the
+        pynvml module is not installed)."""
+        NVML_CLOCK_SM = 1
+        nvmlClocksEventReasonSwPowerCap = 0x4
+        nvmlClocksEventReasonHwSlowdown = 0x8
+        nvmlClocksEventReasonSwThermalSlowdown = 0x20
+        nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+        def __init__(self):
+            import ctypes
+            self.ct = ctypes
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+
+        def _check(self, rc):
+            if rc != 0:
+                raise OSError(f"NVML error {rc}")
+
+        def nvmlDeviceGetHandleByIndex(self, i):
+            h = self.ct.c_void_p()
+            self._check(self.lib.nvmlDeviceGetHandleByIndex_v2(self.ct.c_uint(i), self.ct.byref(h)))
+            return h
+
+        def nvmlDeviceGetHandleByUUID(self, uuid):
+            h = self.ct.c_void_p()
+            self._check(self.lib.nvmlDeviceGetHandleByUUID(self.ct.c_char_p(uuid.encode()), self.ct.byref(h)))
+            return h
+
+        def nvmlDeviceGetClockInfo(self, h, kind):
+            v = self.ct.c_uint()
+            self._check(self.lib.nvmlDeviceGetClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)))
+            return v.value
+
+        def nvmlDeviceGetMaxClockInfo(self, h, kind):
+            v = self.ct.c_uint()
+            self._check(self.lib.nvmlDeviceGetMaxClockInfo(h, self.ct.c_int(kind), self.ct.byref(v)))
+            return v.value
+
+        def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+            v = self.ct.c_ulonglong()
+            f = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self._check(f(h, self.ct.byref(v)))
+            return v.value
+
+    def _nvml_handle(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+        except ImportError:
+            pynvml = self._CNVML()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+        except Exception:
+            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.index)
+
+    def _poll(self):
+        nv, h = self.nv
+        bits = [nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
+                nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap]
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        while not self.stop.is_set():
+            try:
+                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+                r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.samples.append((sm, mx, {n for n, b in zip(self.NAMES, bits) if r & b}))
+            except Exception:
+                break
+            self.stop.wait(0.005)
 
     def __enter__(self):
+        try:
+            import threading
+            self.nv = self._nvml_handle()
+            self.stop = threading.Event()
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+            return self
+        except Exception:
+            self.nv = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "100"],
@@ -126,6 +214,9 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
+        if self.nv is not None:
+            self.stop.set()
+            self.th.join(timeout=5)
         if self.p is not None:
             self.p.terminate()
             try:
@@ -133,29 +224,24 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.p.kill()
                 self.out = ""
+            for line in self.out.strip().splitlines():
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    self.samples.append((float(f[1]), float(f[2]),
+                                         {n for n, v in zip(self.NAMES, f[5:9]) if v.lower().startswith("active")}))
+                except ValueError:
+                    continue
         return False
 
     def summary(self):
-        if self.p is None:
+        if not self.samples:
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.out.strip().splitlines():
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(r for _, _, r in self.samples))
+        return {"sm_mhz": statistics.median(s for s, _, _ in self.samples),
+                "sm_max_mhz": max(m for _, m, _ in self.samples), "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml" if self.nv is not None else "nvidia-smi"}
 
 
 def cpu_baseline(g, replicas):

@@ -99,6 +99,12 @@ def max_over_ranks(dist, x):
     return float(t.item())
 
 
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job rate: every rank processes units_per_rank per step (weak
+    scaling, replicas only), the job's step time is the slowest rank's."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def workload():
     from paper_1909_10547_b300 import workloads as W
     g = W.config3(R=REPLICAS, seed=SEED)
@@ -832,7 +838,7 @@ def main():
     ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
 
     units = fit.ntot * fit.R
-    value = units * world / (ms * 1e-3)
+    value = job_throughput(units, world, ms)
     roof = roofline(fit, seg, args.prec)
     if "step" in seg:
         roof["traffic"] = traffic_of("fit_step", args.prec, fit.ntot, fit.R)
@@ -845,7 +851,7 @@ def main():
             "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
                                                schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves"),
             "roofline": roof,
-            "e2e": {"value": units * world / (ms_e2e * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_throughput(units, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": F_host.numel() * F_host.element_size(),
                     "d2h_bytes_per_step": chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size()},
             "gpu_launches": launches * args.steps, "clocks": clk.summary()}

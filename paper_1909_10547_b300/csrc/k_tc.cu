@@ -324,7 +324,7 @@ enum { MODE_FWD = 0, MODE_ADJ = 1, MODE_DENSE = 2 };
 template <int PREC, int CL>
 size_t tc_smem_bytes(int n_rows) {
     const size_t stage = (size_t)Tr<PREC>::NOPS * Tr<PREC>::ATOMS * (TC_M * 128 + (size_t)(n_rows / CL) * 128);
-    return 1024 + tc_stages<PREC, CL>() * stage + 256;
+    return 1024 + tc_stages<PREC, CL>() * stage + 512;
 }
 
 // One work item is a (replica tile, data tile) pair of the product
@@ -376,6 +376,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto acce = [&](int b) { return bar0 + 8u * (2 * S + 4 + b); };
     const uint32_t drain = bar0 + 8u * (2 * S + 8);  // all MMAs of this CTA done
     uint8_t *gen = smem_raw + (bar0 - raw) + 8 * (2 * S + 9);
+    // group bounds in shared memory (the 256 bytes after the barrier block):
+    // sk[g] = kbeg, sk[NFL + g] = kend, sk[2 * NFL + h] = K of the first
+    // group at or after h whose accumulator the MMA thread waits for (or
+    // INT_MAX); read by the producer and the MMA thread instead of indexing
+    // the kernel parameters at run time
+    int *sk = reinterpret_cast<int *>(smem_raw + (bar0 - raw) + 256);
     // accumulator buffers: NB = 1 << nbl of bcols TMEM columns each; use u of
     // the accumulator is buffer u & NBM, phase u >> nbl of its barriers
     const int nbl = p.nbl, NB = 1 << nbl, NBM = NB - 1;
@@ -401,6 +407,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             prefetch_map(&mapA2);
             prefetch_map(&mapB2);
         }
+    }
+    if (threadIdx.x <= NFL) {
+        const int h = threadIdx.x;
+        if (h < p.ngroups) {
+            sk[h] = p.kbeg[h];
+            sk[NFL + h] = p.kend[h];
+        }
+        const uint32_t mwait = ~p.pwait & ((1u << p.ngroups) - 1u);
+        const uint32_t m = h < p.ngroups ? mwait >> h : 0u;
+        sk[2 * NFL + h] = m ? p.kbeg[h + __ffs(m) - 1] : 0x7fffffff;
     }
     if (warp == 1) tmem_alloc<CL>(smem_u32((const void *)tmem_slot));
     tc_fence_before();
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (leader) {
                     // the accumulator of every group starting in this stage
                     // must be free before the MMAs can read the stage
-                    while (pg < p.ngroups && p.kbeg[pg] < (q + 1) * T::KCS) {
+                    while (pg < p.ngroups && sk[pg] < (q + 1) * T::KCS) {
                         if (((pwait >> pg) & 1u) && !mbar_wait(acce(pgc & NBM), ((pgc >> nbl) & 1) ^ 1, dead)) {
                             ok = false;
                             break;
@@ -506,13 +522,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // with the wait.
         const uint32_t idesc = (1u << 4) | (T::FMT << 7) | (T::FMT << 10) |
                                ((uint32_t)(p.n_rows >> 3) << 17) | ((uint32_t)((CL * TC_M) >> 4) << 24);
-        const uint32_t mwait = ~pwait & ((1u << p.ngroups) - 1u);  // groups the MMA thread waits for
         constexpr int SLOW_UNROLL = T::X3 ? 1 : T::KCS / T::KSTEP;
         // K index where the first MMA-waited group at or after group h starts
-        auto next_wait_k = [&](int h) -> int {
-            const uint32_t m = h < 32 ? mwait >> h : 0u;
-            return m ? p.kbeg[h + __ffs(m) - 1] : 0x7fffffff;
-        };
+        auto next_wait_k = [&](int h) -> int { return sk[2 * NFL + h]; };
         // The issue loop does little besides issuing: the stage's descriptors
         // are built once per stage and a K step only adds its offset to the
         // start-address field (16-byte units; shared-memory addresses stay
@@ -521,13 +533,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t bstep = b_bytes >> 4;           // one B atom, descriptor units
         constexpr uint32_t ASTEP = (TC_M * 128) >> 4;  // one A atom
         const int ng = p.ngroups;
-        const int klast = p.kend[ng - 1];  // K after the last group
+        const int klast = sk[NFL + ng - 1];  // K after the last group
         int it = 0, gc = 0;
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
             // the current group's K range lives in registers; the parameter
             // arrays are read only when a group ends
-            int g = 0, kb = p.kbeg[0], ke = p.kend[0];
+            int g = 0, kb = sk[0], ke = sk[NFL];
             int kw = next_wait_k(0);
             uint32_t d = tmem + (uint32_t)(gc & NBM) * bcols;
             for (int q = 0; q < p.nchunks && ok; ++q, ++it) {
@@ -564,8 +576,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             ++g;
                             d = tmem + (uint32_t)(gc & NBM) * bcols;
                             if (g < ng) {
-                                kb = p.kbeg[g];
-                                ke = p.kend[g];
+                                kb = sk[g];
+                                ke = sk[NFL + g];
                             }
                         }
                     }
@@ -604,8 +616,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             ++g;
                             d = tmem + (uint32_t)(gc & NBM) * bcols;
                             if (g < ng) {
-                                kb = p.kbeg[g];
-                                ke = p.kend[g];
+                                kb = sk[g];
+                                ke = sk[NFL + g];
                             }
                         }
                     }

@@ -169,7 +169,7 @@ int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
  * fk: HOST [ndata][K] doubles, copied into device memory the table owns, in
  * the precisions of prec_mask (FP64, FP32, BF16, BF16 hi+lo, TF32).
  * fk_table_info reports kind FK_KIND_DENSE, nchannels = nx = nx_grid = 0.
- * Errors: FK_EINVAL (NULL, ndata < 1, K < 1 or K > 2^31 - 1024, bad mask),
+ * Errors: FK_EINVAL (NULL, ndata < 1, K < 1 or K > 2^30, bad mask),
  * FK_ENOMEM, FK_ECUDA.
  */
 int fk_table_create_dense(const double *fk, int ndata, long long K, unsigned prec_mask,

@@ -176,7 +176,7 @@ int dense_create(const double *fk, int ndata, long long K, unsigned mask, fk_tab
     *out = nullptr;
     if (!fk) return fail(FK_EINVAL, "null table");
     if (ndata < 1) return fail(FK_EINVAL, "ndata < 1");
-    if (K < 1 || K > (1LL << 31) - 1024) return fail(FK_EINVAL, "K must be in 1..2^31-1024");
+    if (K < 1 || K > (1LL << 30)) return fail(FK_EINVAL, "K must be in 1..2^30");
     if (!mask || (mask & ~ALL_PRECS)) return fail(FK_EINVAL, "bad precision mask");
     keep_pool();
     fk_table *t = new fk_table();

@@ -80,3 +80,14 @@ def test_dense_and_luminosity_reject_null_handles():
     lib = _lib.load()
     assert lib.fk_dense_conv(None, None, 1, None, 0, 0, None) == _lib.FK_EINVAL
     assert lib.fk_luminosity(None, None, 1, None, 0, None) == _lib.FK_EINVAL
+
+
+def test_dense_table_k_limit_needs_no_gpu():
+    import ctypes
+    import numpy as np
+    lib = _lib.load()
+    buf = np.zeros(4)
+    out = ctypes.c_void_p()
+    # the limit is checked before the table is read
+    assert lib.fk_table_create_dense(buf.ctypes.data_as(ctypes.c_void_p), 1, (1 << 30) + 1,
+                                     1 << _lib.FK_FP32, ctypes.byref(out)) == _lib.FK_EINVAL

@@ -180,7 +180,10 @@ int fk_table_create_dense(const double *fk, int ndata, long long K, unsigned pre
  * FK_FP64, float otherwise; the reduced modes round it to the mode, as F in
  * fk_had_conv).  O: DEVICE, as in fk_had_conv (ldo = 0: [R][ndata]),
  * overwritten.  FP64 and FP32 run on the CUDA cores, BF16 / BF16 hi+lo / TF32
- * on the tensor cores with FP32 accumulation.  Asynchronous on stream.
+ * on the tensor cores with FP32 accumulation.  Asynchronous on stream.  The
+ * summation order depends on R (the streaming kernel serves R <= 4, and the
+ * tensor-core modes split K when the tiles leave SMs idle), so unlike
+ * fk_had_conv a replica's last bits may differ between calls with different R.
  * Errors: as fk_had_conv (a table of another kind: FK_EINVAL).
  */
 int fk_dense_conv(const fk_table *t, const void *L, int R, void *O, int ldo, int prec,

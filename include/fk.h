@@ -260,11 +260,12 @@ int fk_grad_sum(const void *const *parts, int nparts, long long n, void *out, in
 /*
  * Block-diagonal experimental covariance, one dense SPD block per dataset.
  * C_blocks: HOST FP64, the blocks one after another, each row-major
- * [n_k][n_k]; block_sizes: HOST [nblocks].  The blocks are copied to the
- * device and factorised there in FP64 (C_k = L_k L_k^T), and each L_k is
- * inverted by triangular solves against the identity.  The call synchronises
- * with the device.  Errors: FK_EINVAL (sizes, or a block that is not
- * positive definite: a non-positive pivot), FK_ENOMEM, FK_ECUDA.
+ * [n_k][n_k]; block_sizes: HOST [nblocks], each 1 .. 46340, their sum at most
+ * 2^30.  The blocks are copied to the device and factorised there in FP64
+ * (C_k = L_k L_k^T); the 32 x 32 diagonal blocks of L_k (and of L_k^T read
+ * backwards) are inverted for the blocked substitutions of fk_chi2.  The call
+ * synchronises with the device.  Errors: FK_EINVAL (sizes, or a block that is
+ * not positive definite: a non-positive pivot), FK_ENOMEM, FK_ECUDA.
  */
 int fk_cov_create(const double *C_blocks, const int *block_sizes, int nblocks, fk_cov **out);
 int fk_cov_destroy(fk_cov *cov);
@@ -273,8 +274,12 @@ int fk_cov_size(const fk_cov *cov);
 
 /*
  * chi^2 per replica: chi2[r] = (O_r - D)^T C^{-1} (O_r - D), evaluated in
- * FP64 as |L^{-1}(O_r - D)|^2 blockwise.  If gO is not NULL it receives
- * d chi2[r] / d O_r = 2 C^{-1} (O_r - D).
+ * FP64 as |z|^2 blockwise, z the solution of L z = O_r - D by blocked forward
+ * substitution (panels of 32 rows).  If gO is not NULL it receives
+ * d chi2[r] / d O_r = 2 C^{-1} (O_r - D) = 2 w, w the solution of L^T w = z
+ * by blocked back substitution.  One kernel launch per call (two when the
+ * covariance has several blocks: their chi^2 are then added in block order);
+ * a replica's results do not depend on R or on the other replicas.
  * O: DEVICE [R][n] and gO: DEVICE [R][n] or NULL, both double if io_prec is
  * FK_FP64 and float for any other mode (so the observables and gradient of a
  * reduced-precision fit need no conversion; the arithmetic is FP64 either

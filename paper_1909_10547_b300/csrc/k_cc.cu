@@ -960,20 +960,44 @@ static __device__ __align__(256) unsigned char g_fk_noalloc_scratch[FK_NOALLOC_B
 namespace fk {
 namespace {
 
+// The driver's current context, through the runtime's entry-point query (the
+// library does not link the driver API); NULL if the query is unavailable.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(ptr);
+    });
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
+
 // Device address of g_fk_noalloc_scratch on the current device.  The first
-// call on a device performs the lookup (so make it before any stream capture).
+// call on a device performs the lookup (so make it before any stream capture);
+// the address is kept with the context it belongs to and looked up again if
+// the device's context has changed since.
 int noalloc_scratch(void **out) {
     static std::mutex mu;
     static void *addr[256] = {};
+    static CUcontext ctx[256] = {};
     int dev = 0;
     FK_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return fail(FK_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    const CUcontext now = current_context();
+    if (!addr[dev] || ctx[dev] != now) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_fk_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
         addr[dev] = p;
+        ctx[dev] = current_context();
     }
     *out = addr[dev];
     return FK_OK;

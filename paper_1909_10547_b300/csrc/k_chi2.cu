@@ -4,35 +4,51 @@
 // convolution turns into the gradient with respect to the PDF (the fit of
 // Sec. 2 is gradient descent).
 //
-// Set-up (fk_cov_create, once): C_k = L_k L_k^T by a column-wise (left-looking)
-// Cholesky, then X_k = L_k^{-1} by forward substitution against the identity.
-// Per call: z = X_k (O_r - D) (the triangular solve L_k z = O_r - D, applied as
-// a product with the precomputed inverse so that every row is independent),
-// chi2 = |z|^2, gO = 2 X_k^T z.  Sums over rows use fixed-order partials.
+// Set-up (fk_cov_create, once per covariance):
+//   C_k = L_k L_k^T by a column-wise (left-looking) Cholesky, kept row-major
+//   and transposed (LT = L^T, row-major: column m of L is contiguous);
+//   the inverses of the 32 x 32 diagonal blocks of L_k and of its "reversed
+//   transpose" U[i][m] = L[n-1-m][n-1-i] (lower triangular), each by
+//   substitution against the identity.
+// Per call (one kernel, k_chi2_solve): blocked forward substitution
+// L z = O_r - D over panels of 32 rows (the usual TRSM arrangement): the
+// panel's rows first take the contributions of every earlier row,
+// t_i = r_i - sum_{m < i0} L[i][m] z_m, then its own triangle is applied
+// through its inverted diagonal block.  chi2 = |z|^2.  The back substitution
+// L^T w = z is the same forward substitution on U with reversed vectors
+// (w'_i = w_{n-1-i}), and gO = 2 w.  In the update one lane owns one row of
+// the panel and the CTA's warps split the columns m, so every load of L is a
+// coalesced row of LT (or, reversed, of L) and each lane's partial sums stay
+// in registers; the eight warp partials are added in warp order.  One CTA owns
+// one covariance block and a few replicas, keeps their vectors in shared
+// memory and writes chi^2 and gO directly: every sum runs in an order that
+// depends only on the block size, never on R or on the replica tile.
 #include "fk_internal.h"
 
 #include <algorithm>
 #include <cmath>
 
 struct fk_cov {
-    int nblocks = 0, n = 0;
+    int nblocks = 0, n = 0, maxn = 0;
     std::vector<int> sizes, offs;
-    std::vector<long long> loff;
+    std::vector<long long> loff, doff;
     int *d_sizes = nullptr, *d_offs = nullptr;
-    long long *d_loff = nullptr;
-    int ntiles = 0;
-    int *d_tile_blk = nullptr, *d_tile_i0 = nullptr;
-    int nzu = 0, ngu = 0;                          // work units of the two passes
-    int *d_zu = nullptr, *d_gu = nullptr, *d_zt = nullptr, *d_gt = nullptr;
-    double *L = nullptr;     // per block n_k x n_k row-major, lower factor
-    double *Linv = nullptr;  // same layout, L^{-1} (lower)
+    long long *d_loff = nullptr, *d_doff = nullptr;
+    double *L = nullptr;   // per block n_k x n_k row-major, lower factor
+    double *LT = nullptr;  // per block, L^T row-major
+    double *DL = nullptr;  // per block, per 32-row panel: inverse of L's diagonal block, column-major 32 x 32
+    double *DU = nullptr;  // the same for U
     size_t bytes = 0;
 };
 
 namespace fk {
 namespace {
 
-constexpr int CT = 32;  // tile of rows / replicas
+constexpr int PB = 32;          // rows per panel
+constexpr int SOLVE_THREADS = 256;
+constexpr int SOLVE_WARPS = SOLVE_THREADS / 32;
+// a block's vectors stay in shared memory up to this many doubles per CTA
+constexpr int SMEM_VEC_DOUBLES = 3072;  // 24 KB (with the 8 + 16 KB of static panel buffers, within 48 KB)
 
 // One CTA per block.  In: A = C_k.  Out: A = L_k (zeros above the diagonal).
 __global__ void __launch_bounds__(256) k_chol(const long long *__restrict__ loff,
@@ -81,182 +97,179 @@ __global__ void __launch_bounds__(256) k_chol(const long long *__restrict__ loff
     }
 }
 
-// grid (nblocks, ceil(maxn/128)); thread = one column m of X = L^{-1}.
-__global__ void __launch_bounds__(128) k_trinv(const long long *__restrict__ loff,
-                                               const int *__restrict__ sizes,
-                                               const double *__restrict__ L, double *__restrict__ X) {
+// grid (nblocks, 64): LT[m][i] = L[i][m]
+__global__ void __launch_bounds__(256) k_transpose(const long long *__restrict__ loff, const int *__restrict__ sizes,
+                                                   const double *__restrict__ L, double *__restrict__ LT) {
     const int k = blockIdx.x, n = sizes[k];
-    const int m = blockIdx.y * blockDim.x + threadIdx.x;
-    if (m >= n) return;
     const double *Lk = L + loff[k];
-    double *Xk = X + loff[k];
-    for (int i = 0; i < m; ++i) Xk[(size_t)i * n + m] = 0.0;
-    Xk[(size_t)m * n + m] = 1.0 / Lk[(size_t)m * n + m];
-    for (int i = m + 1; i < n; ++i) {
-        double s = 0.0;
-        for (int q = m; q < i; ++q) s = fma(Lk[(size_t)i * n + q], Xk[(size_t)q * n + m], s);
-        Xk[(size_t)i * n + m] = -s / Lk[(size_t)i * n + i];
+    double *Tk = LT + loff[k];
+    const size_t nn = (size_t)n * n;
+    for (size_t idx = (size_t)blockIdx.y * 256 + threadIdx.x; idx < nn; idx += (size_t)gridDim.y * 256) {
+        const int m = (int)(idx / n), i = (int)(idx % n);
+        Tk[idx] = Lk[(size_t)i * n + m];
     }
 }
 
-// A tile is 32 rows i0.. of one block.  Its contraction range is cut into
-// work units of at most UNIT_COLS columns so that no CTA carries a long chain
-// (the FP64 pipe is shared by the CTAs of an SM; one long tile would set the
-// kernel's length); the units' partial sums are added in unit order.
-constexpr int UNIT_COLS = 4 * CT;
+// grid (nblocks, max panels, 2), 32 threads: thread c solves B x = e_c for the
+// panel's diagonal block B (rows and columns i0 .. i0 + rows - 1 of L, or for
+// blockIdx.z = 1 of U[i][m] = L[n-1-m][n-1-i]) and stores column c of B^{-1}
+// at Dinv[p][c][0..32) (zeros above the diagonal and outside the block).
+__global__ void __launch_bounds__(32) k_dinv(const long long *__restrict__ loff, const long long *__restrict__ doff,
+                                             const int *__restrict__ sizes, const double *__restrict__ L,
+                                             double *__restrict__ DL, double *__restrict__ DU) {
+    const int k = blockIdx.x, p = blockIdx.y, n = sizes[k];
+    const int i0 = p * PB;
+    if (i0 >= n) return;
+    const int rows = min(PB, n - i0);
+    const double *Lk = L + loff[k];
+    const bool rev = blockIdx.z != 0;
+    auto el = [&](int i, int m) {  // element (i, m) of L or of U
+        return rev ? Lk[(size_t)(n - 1 - m) * n + (n - 1 - i)] : Lk[(size_t)i * n + m];
+    };
+    double *out = (rev ? DU : DL) + doff[k] + (size_t)p * PB * PB;
+    const int c = threadIdx.x;
+    double x[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) x[i] = 0.0;
+    if (c < rows) {
+        for (int i = c; i < rows; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = c; q < i; ++q) s = fma(-el(i0 + i, i0 + q), x[q], s);
+            x[i] = s / el(i0 + i, i0 + i);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PB; ++i) out[c * PB + i] = x[i];
+}
 
 struct CovView {
     int n;
-    const int *sizes, *offs, *tile_blk, *tile_i0;
-    const long long *loff;
-    const double *Linv;
-    const int *zu, *gu;     // units [u][3]: tile, m0, m1 (z pass, gradient pass)
-    const int *zt, *gt;     // per tile [t][2]: first unit, unit count
+    const int *sizes, *offs;
+    const long long *loff, *doff;
+    const double *L, *LT, *DL, *DU;
 };
 
-// grid (nunits, ceil(R/32)), 256 threads: thread (ty, tx) -> rows i0+ty*4+p, replica r0+tx.
-// Zp[(u*32 + row)*R + r] = sum_{m in [m0, m1)} X[i][m] (O[r][off+m] - D[off+m])
-template <typename TO>
-__global__ void __launch_bounds__(256) k_chi2_zpart(CovView cv, const TO *__restrict__ O,
-                                                    const double *__restrict__ D, int R,
-                                                    double *__restrict__ Zp) {
-    const int u = blockIdx.x, tile = cv.zu[3 * u], m0u = cv.zu[3 * u + 1], m1u = cv.zu[3 * u + 2];
-    const int k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
-    const int nk = cv.sizes[k], off = cv.offs[k];
-    const double *X = cv.Linv + cv.loff[k];
-    const int r0 = blockIdx.y * CT;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    __shared__ double Ls[CT][CT + 1], Rs[CT][CT + 1];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int m0 = m0u; m0 < m1u; m0 += CT) {
-        for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
-            const int a = idx / CT, b = idx % CT;
-            const int i = i0 + a, m = m0 + b;
-            Ls[a][b] = (i < nk && m < m1u) ? X[(size_t)i * nk + m] : 0.0;
-            const int r = r0 + a;
-            Rs[b][a] = (r < R && m < m1u) ? (double)O[(size_t)r * cv.n + off + m] - D[off + m] : 0.0;
+__device__ __forceinline__ double warp_sum(double v) {
+    // xor butterfly: every lane ends with the same value (each level adds the
+    // same two numbers in every lane, and addition is commutative)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Solves M y = b in place for RT right-hand sides, M lower triangular n x n
+// with element (i, m) at P[m * sm + i * si], b / y in v[rr * n + idx(i)]
+// (idx(i) = i, or n - 1 - i when REV: the reversed vectors of the back
+// substitution).  Dinv holds the inverted diagonal blocks of M.  Shared
+// memory: part [SOLVE_WARPS][RT][32] for the warp partials, Ds [32 * 32] for
+// the panel's inverted diagonal block.
+template <int RT, bool REV>
+__device__ void blocked_solve(const double *__restrict__ P, long long sm, long long si,
+                              const double *__restrict__ Dinv, int n, double *v,
+                              double (*part)[RT][PB], double *Ds) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto at = [&](int rr, int i) -> double & { return v[rr * n + (REV ? n - 1 - i : i)]; };
+    for (int i0 = 0; i0 < n; i0 += PB) {
+        const int rows = min(PB, n - i0);
+        const bool own = lane < rows;  // lane owns row i0 + lane
+        // the panel's Dinv block to shared memory; its loads overlap the update
+        const double *Dp = Dinv + (size_t)(i0 / PB) * PB * PB;
+        for (int e = threadIdx.x; e < PB * PB; e += SOLVE_THREADS) Ds[e] = __ldg(Dp + e);
+        const double *Pi = P + (long long)(i0 + (own ? lane : 0)) * si;
+        // columns [0, i0) in SOLVE_WARPS chunks of `per`; four interleaved
+        // accumulators per replica keep the dependent chains short
+        const int per = (i0 + SOLVE_WARPS - 1) / SOLVE_WARPS;
+        const int m0 = warp * per, m1 = min(i0, m0 + per);
+        double acc[RT][4];
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[rr][u] = 0.0;
+        int m = m0;
+        for (; m + 4 <= m1; m += 4) {
+            double a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = own ? __ldg(Pi + (long long)(m + u) * sm) : 0.0;
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[rr][u] = fma(a[u], at(rr, m + u), acc[rr][u]);
+        }
+        for (; m < m1; ++m) {
+            const double a = own ? __ldg(Pi + (long long)m * sm) : 0.0;
+#pragma unroll
+            for (int rr = 0; rr < RT; ++rr) acc[rr][0] = fma(a, at(rr, m), acc[rr][0]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < RT; ++rr) part[warp][rr][lane] = (acc[rr][0] + acc[rr][1]) + (acc[rr][2] + acc[rr][3]);
+        __syncthreads();
+        // warp rr: t = b - (sum of the warp partials, in warp order), then
+        // y_panel = Dinv_p t (Dinv_p column-major, zero above its diagonal and
+        // outside the panel, so all 32 columns can be summed)
+        for (int rr = warp; rr < RT; rr += SOLVE_WARPS) {
+            double sum = part[0][rr][lane];
+#pragma unroll
+            for (int w = 1; w < SOLVE_WARPS; ++w) sum += part[w][rr][lane];
+            const double t = own ? at(rr, i0 + lane) - sum : 0.0;
+            double s4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < PB; ++c) s4[c & 3] = fma(Ds[c * PB + lane], __shfl_sync(0xffffffffu, t, c), s4[c & 3]);
+            if (own) at(rr, i0 + lane) = (s4[0] + s4[1]) + (s4[2] + s4[3]);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int mm = 0; mm < CT; ++mm) {
-            const double rv = Rs[mm][tx];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) acc[p] = fma(Ls[ty * 4 + p][mm], rv, acc[p]);
-        }
-        __syncthreads();
-    }
-    const int r = r0 + tx;
-    if (r < R) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) Zp[((size_t)u * CT + ty * 4 + p) * R + r] = acc[p];
     }
 }
 
-// grid (ntiles, ceil(R/32)): Z = sum of the tile's unit partials (in order),
-// zsq[tile*R + r] = sum over the tile's rows of Z^2.
-__global__ void __launch_bounds__(256) k_chi2_zred(CovView cv, const double *__restrict__ Zp, int R,
-                                                   double *__restrict__ Z, double *__restrict__ zsq) {
-    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
-    const int nk = cv.sizes[k], off = cv.offs[k];
-    const int u0 = cv.zt[2 * tile], nu = cv.zt[2 * tile + 1];
-    const int r = blockIdx.y * CT + (threadIdx.x & 31), ty = threadIdx.x >> 5;
-    __shared__ double sq[8][CT];
-    double s = 0.0;
-    if (r < R) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int row = ty * 4 + p, i = i0 + row;
-            double z = 0.0;
-            for (int u = 0; u < nu; ++u) z += Zp[((size_t)(u0 + u) * CT + row) * R + r];
-            if (i < nk) {
-                Z[(size_t)(off + i) * R + r] = z;
-                s = fma(z, z, s);
-            }
-        }
+// grid (nblocks, replica tiles of RT from rfirst), SOLVE_THREADS threads.  vg: global scratch for
+// the vectors when a block is too large for shared memory (else NULL).
+// chi2 of the block goes to out[k * R + r] (or straight to chi2[r] when the
+// covariance has one block: out = chi2).
+template <typename TO, int RT>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_chi2_solve(CovView cv, const TO *__restrict__ O,
+                                                              const double *__restrict__ D, int R, int rfirst,
+                                                              double *__restrict__ out, TO *__restrict__ gO,
+                                                              double *__restrict__ vg) {
+    const int k = blockIdx.x, n = cv.sizes[k], off = cv.offs[k];
+    const int r0 = rfirst + blockIdx.y * RT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    extern __shared__ double smem_v[];
+    __shared__ double part[SOLVE_WARPS][RT][PB];
+    __shared__ double Ds[PB * PB];
+    double *v = vg ? vg + ((size_t)blockIdx.y * gridDim.x + k) * RT * (size_t)n : smem_v;
+    for (int idx = threadIdx.x; idx < RT * n; idx += SOLVE_THREADS) {
+        const int rr = idx / n, i = idx - rr * n, r = r0 + rr;
+        v[idx] = r < R ? (double)O[(size_t)r * cv.n + off + i] - D[off + i] : 0.0;
     }
-    sq[ty][threadIdx.x & 31] = s;
     __syncthreads();
-    if (ty == 0 && r < R) {
-        double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += sq[q][threadIdx.x];
-        zsq[(size_t)tile * R + r] = t;
+    const double *Lk = cv.L + cv.loff[k];
+    // forward: L[i][m] = LT[m * n + i]
+    blocked_solve<RT, false>(cv.LT + cv.loff[k], n, 1, cv.DL + cv.doff[k], n, v, part, Ds);
+    for (int rr = warp; rr < RT; rr += SOLVE_WARPS) {
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s = fma(v[rr * n + i], v[rr * n + i], s);
+        s = warp_sum(s);
+        if (lane == 0 && r0 + rr < R) out[(size_t)k * R + r0 + rr] = s;
+    }
+    if (!gO) return;
+    // back: U[i][m] = L[n-1-m][n-1-i] = Lk[(n-1)(n+1) - m n - i]
+    blocked_solve<RT, true>(Lk + (long long)(n - 1) * (n + 1), -(long long)n, -1, cv.DU + cv.doff[k], n, v, part, Ds);
+    for (int idx = threadIdx.x; idx < RT * n; idx += SOLVE_THREADS) {
+        const int rr = idx / n, i = idx - rr * n, r = r0 + rr;
+        if (r < R) gO[(size_t)r * cv.n + off + i] = (TO)(2.0 * v[idx]);
     }
 }
 
-// chi2[r] = sum_tile zsq[tile][r], tiles in order.
-__global__ void k_chi2_sum(const double *__restrict__ zsq, int ntiles, int R, double *__restrict__ chi2) {
+// chi2[r] = sum_k zsq[k][r], blocks in order.
+__global__ void k_chi2_sum(const double *__restrict__ zsq, int nblocks, int R, double *__restrict__ chi2) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     double s = 0.0;
-    for (int t = 0; t < ntiles; ++t) s += zsq[(size_t)t * R + r];
+    for (int k = 0; k < nblocks; ++k) s += zsq[(size_t)k * R + r];
     chi2[r] = s;
 }
 
-// grid (nunits, ceil(R/32)): Gp[(u*32 + row)*R + r] = sum_{m in [m0, m1)} X[m][i] Z[off+m][r]
-__global__ void __launch_bounds__(256) k_chi2_gpart(CovView cv, const double *__restrict__ Z, int R,
-                                                    double *__restrict__ Gp) {
-    const int u = blockIdx.x, tile = cv.gu[3 * u], m0u = cv.gu[3 * u + 1], m1u = cv.gu[3 * u + 2];
-    const int k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
-    const int nk = cv.sizes[k], off = cv.offs[k];
-    const double *X = cv.Linv + cv.loff[k];
-    const int r0 = blockIdx.y * CT;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    __shared__ double Ls[CT][CT + 1], Zs[CT][CT + 1];
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int m0 = m0u; m0 < m1u; m0 += CT) {
-        for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
-            const int a = idx / CT, b = idx % CT;
-            const int m = m0 + a, i = i0 + b;
-            Ls[a][b] = (m < m1u && i < nk) ? X[(size_t)m * nk + i] : 0.0;
-            const int r = r0 + b;
-            Zs[a][b] = (m < m1u && r < R) ? Z[(size_t)(off + m) * R + r] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int mm = 0; mm < CT; ++mm) {
-            const double zv = Zs[mm][tx];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) acc[p] = fma(Ls[mm][ty * 4 + p], zv, acc[p]);
-        }
-        __syncthreads();
-    }
-    const int r = r0 + tx;
-    if (r < R) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) Gp[((size_t)u * CT + ty * 4 + p) * R + r] = acc[p];
-    }
-}
-
-// grid (ntiles, ceil(R/32)): gO[r][off+i] = 2 * sum of the tile's unit partials (in order)
-template <typename TO>
-__global__ void __launch_bounds__(256) k_chi2_gred(CovView cv, const double *__restrict__ Gp, int R,
-                                                   TO *__restrict__ gO) {
-    const int tile = blockIdx.x, k = cv.tile_blk[tile], i0 = cv.tile_i0[tile];
-    const int nk = cv.sizes[k], off = cv.offs[k];
-    const int u0 = cv.gt[2 * tile], nu = cv.gt[2 * tile + 1];
-    const int r0 = blockIdx.y * CT;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    __shared__ double out[CT][CT + 1];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int row = ty * 4 + p;
-        double g = 0.0;
-        if (r0 + tx < R)
-            for (int u = 0; u < nu; ++u) g += Gp[((size_t)(u0 + u) * CT + row) * R + r0 + tx];
-        out[tx][row] = 2.0 * g;
-    }
-    __syncthreads();
-    // stage for coalesced stores along i
-    for (int idx = threadIdx.x; idx < CT * CT; idx += 256) {
-        const int rr = idx / CT, ii = idx % CT;
-        const int r = r0 + rr, i = i0 + ii;
-        if (r < R && i < nk) gO[(size_t)r * cv.n + off + i] = (TO)out[rr][ii];
-    }
-}
-
 CovView cview(const fk_cov *c) {
-    return CovView{c->n, c->d_sizes, c->d_offs, c->d_tile_blk, c->d_tile_i0, c->d_loff, c->Linv,
-                   c->d_zu, c->d_gu, c->d_zt, c->d_gt};
+    return CovView{c->n, c->d_sizes, c->d_offs, c->d_loff, c->d_doff, c->L, c->LT, c->DL, c->DU};
 }
 
 void cov_free(fk_cov *c) {
@@ -264,33 +277,12 @@ void cov_free(fk_cov *c) {
     cudaFree(c->d_sizes);
     cudaFree(c->d_offs);
     cudaFree(c->d_loff);
-    cudaFree(c->d_tile_blk);
-    cudaFree(c->d_tile_i0);
-    cudaFree(c->d_zu);
-    cudaFree(c->d_gu);
-    cudaFree(c->d_zt);
-    cudaFree(c->d_gt);
+    cudaFree(c->d_doff);
     cudaFree(c->L);
-    cudaFree(c->Linv);
+    cudaFree(c->LT);
+    cudaFree(c->DL);
+    cudaFree(c->DU);
     delete c;
-}
-
-// Work units of the two passes: z needs columns [0, min(i0+32, n)) of the
-// tile's rows, the gradient columns [i0, n); each range cut every UNIT_COLS.
-void make_units(const std::vector<int> &tb, const std::vector<int> &ti, const std::vector<int> &sizes,
-                bool grad, std::vector<int> &units, std::vector<int> &per_tile) {
-    for (size_t t = 0; t < tb.size(); ++t) {
-        const int n = sizes[tb[t]], i0 = ti[t];
-        const int b = grad ? i0 : 0, e = grad ? n : std::min(i0 + CT, n);
-        per_tile.push_back((int)(units.size() / 3));
-        int cnt = 0;
-        for (int m = b; m < e; m += UNIT_COLS, ++cnt) {
-            units.push_back((int)t);
-            units.push_back(m);
-            units.push_back(std::min(m + UNIT_COLS, e));
-        }
-        per_tile.push_back(cnt);
-    }
 }
 
 int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
@@ -298,41 +290,42 @@ int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
     *out = nullptr;
     fk_cov *c = new fk_cov();
     c->nblocks = nb;
-    long long tot = 0, el = 0;
-    int maxn = 0;
-    std::vector<int> tb, ti;
+    long long tot = 0, el = 0, dl = 0;
+    int maxp = 0;
     for (int k = 0; k < nb; ++k) {
         if (bs[k] < 1) {
             delete c;
             return fail(FK_EINVAL, "fk_cov_create: block size < 1");
         }
+        if (bs[k] > 46340) {  // n * n must stay within 32-bit element offsets per row product
+            delete c;
+            return fail(FK_EINVAL, "fk_cov_create: block size > 46340");
+        }
+        if (tot + bs[k] > (1LL << 30)) {
+            delete c;
+            return fail(FK_EINVAL, "fk_cov_create: dimension too large");
+        }
         c->sizes.push_back(bs[k]);
         c->offs.push_back((int)tot);
         c->loff.push_back(el);
-        for (int i0 = 0; i0 < bs[k]; i0 += CT) {
-            tb.push_back(k);
-            ti.push_back(i0);
-        }
+        c->doff.push_back(dl);
+        const int np = (bs[k] + PB - 1) / PB;
         tot += bs[k];
         el += (long long)bs[k] * bs[k];
-        maxn = std::max(maxn, bs[k]);
-    }
-    if (tot > (1LL << 30)) {
-        delete c;
-        return fail(FK_EINVAL, "fk_cov_create: dimension too large");
+        dl += (long long)np * PB * PB;
+        c->maxn = std::max(c->maxn, bs[k]);
+        maxp = std::max(maxp, np);
     }
     c->n = (int)tot;
-    c->ntiles = (int)tb.size();
-    c->bytes = sizeof(double) * 2 * el;
+    c->bytes = sizeof(double) * (2 * el + 2 * dl);
     auto cleanup = [&](int st) {
         cov_free(c);
         return st;
     };
     if (cudaMalloc(&c->d_sizes, sizeof(int) * nb) || cudaMalloc(&c->d_offs, sizeof(int) * nb) ||
-        cudaMalloc(&c->d_loff, sizeof(long long) * nb) ||
-        cudaMalloc(&c->d_tile_blk, sizeof(int) * c->ntiles) ||
-        cudaMalloc(&c->d_tile_i0, sizeof(int) * c->ntiles) || cudaMalloc(&c->L, sizeof(double) * el) ||
-        cudaMalloc(&c->Linv, sizeof(double) * el))
+        cudaMalloc(&c->d_loff, sizeof(long long) * nb) || cudaMalloc(&c->d_doff, sizeof(long long) * nb) ||
+        cudaMalloc(&c->L, sizeof(double) * el) || cudaMalloc(&c->LT, sizeof(double) * el) ||
+        cudaMalloc(&c->DL, sizeof(double) * dl) || cudaMalloc(&c->DU, sizeof(double) * dl))
         return cleanup(fail(FK_ENOMEM, "fk_cov_create: device allocation failed"));
     int *d_info = nullptr;
     if (cudaMalloc(&d_info, sizeof(int) * nb)) return cleanup(fail(FK_ENOMEM, "fk_cov_create: info"));
@@ -340,23 +333,8 @@ int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
     e = e ? e : cudaMemcpy(c->d_sizes, c->sizes.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->d_offs, c->offs.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->d_loff, c->loff.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(c->d_tile_blk, tb.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(c->d_tile_i0, ti.data(), sizeof(int) * c->ntiles, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(c->d_doff, c->doff.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(c->L, C, sizeof(double) * el, cudaMemcpyHostToDevice);
-    std::vector<int> zu, zt, gu, gt;
-    make_units(tb, ti, c->sizes, false, zu, zt);
-    make_units(tb, ti, c->sizes, true, gu, gt);
-    c->nzu = (int)zu.size() / 3;
-    c->ngu = (int)gu.size() / 3;
-    if (!e && (cudaMalloc(&c->d_zu, sizeof(int) * zu.size()) || cudaMalloc(&c->d_gu, sizeof(int) * gu.size()) ||
-               cudaMalloc(&c->d_zt, sizeof(int) * zt.size()) || cudaMalloc(&c->d_gt, sizeof(int) * gt.size()))) {
-        cudaFree(d_info);
-        return cleanup(fail(FK_ENOMEM, "fk_cov_create: work units"));
-    }
-    e = e ? e : cudaMemcpy(c->d_zu, zu.data(), sizeof(int) * zu.size(), cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(c->d_gu, gu.data(), sizeof(int) * gu.size(), cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(c->d_zt, zt.data(), sizeof(int) * zt.size(), cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(c->d_gt, gt.data(), sizeof(int) * gt.size(), cudaMemcpyHostToDevice);
     if (e) {
         cudaFree(d_info);
         return cleanup(cuda_fail(e, "fk_cov_create: copy"));
@@ -364,12 +342,6 @@ int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
     k_chol<<<nb, 256>>>(c->d_loff, c->d_sizes, c->L, d_info);
     count_launch();
     e = cudaGetLastError();
-    dim3 g2(nb, (maxn + 127) / 128);
-    if (!e) {
-        k_trinv<<<g2, 128>>>(c->d_loff, c->d_sizes, c->L, c->Linv);
-        count_launch();
-    }
-    e = e ? e : cudaGetLastError();
     std::vector<int> info(nb, 0);
     e = e ? e : cudaMemcpy(info.data(), d_info, sizeof(int) * nb, cudaMemcpyDeviceToHost);
     cudaFree(d_info);
@@ -379,38 +351,68 @@ int cov_create(const double *C, const int *bs, int nb, fk_cov **out) {
             return cleanup(fail(FK_EINVAL, "fk_cov_create: block " + std::to_string(k) +
                                                " is not positive definite (pivot " +
                                                std::to_string(info[k] - 1) + ")"));
+    k_transpose<<<dim3(nb, 64), 256>>>(c->d_loff, c->d_sizes, c->L, c->LT);
+    count_launch();
+    e = cudaGetLastError();
+    if (!e) {
+        k_dinv<<<dim3(nb, maxp, 2), 32>>>(c->d_loff, c->d_doff, c->d_sizes, c->L, c->DL, c->DU);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    e = e ? e : cudaDeviceSynchronize();
+    if (e) return cleanup(cuda_fail(e, "fk_cov_create: diagonal blocks"));
     *out = c;
     return FK_OK;
 }
 
-template <typename TO>
-int chi2_t(const fk_cov *c, const TO *O, const double *D, int R, double *out, TO *gO,
-           cudaStream_t s) {
-    Scratch scr(s);
-    double *Z = nullptr, *zsq = nullptr, *part = nullptr;
-    FK_CUDA(scr.get(&Z, (size_t)c->n * R));
-    FK_CUDA(scr.get(&zsq, (size_t)c->ntiles * R));
-    FK_CUDA(scr.get(&part, (size_t)std::max(c->nzu, c->ngu) * CT * R));
-    CovView cv = cview(c);
-    const int rt = (R + CT - 1) / CT;
-    k_chi2_zpart<TO><<<dim3(c->nzu, rt), 256, 0, s>>>(cv, O, D, R, part);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    k_chi2_zred<<<dim3(c->ntiles, rt), 256, 0, s>>>(cv, part, R, Z, zsq);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    k_chi2_sum<<<(R + 127) / 128, 128, 0, s>>>(zsq, c->ntiles, R, out);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    if (gO) {
-        k_chi2_gpart<<<dim3(c->ngu, rt), 256, 0, s>>>(cv, Z, R, part);
+// Replicas per CTA: as many as keep one CTA's FP64 work (n^2 * RT
+// multiply-adds for the two substitutions) within 2^16, so that the chain of
+// a block stays short and its replicas spread over many SMs, with the vectors
+// of RT replicas within the shared-memory budget.
+int pick_rt(int maxn) {
+    const long long nn = (long long)maxn * maxn;
+    for (int rt : {8, 4, 2})
+        if (nn * rt <= (1LL << 16) && (long long)rt * maxn <= SMEM_VEC_DOUBLES) return rt;
+    return 1;
+}
+
+template <typename TO, int RT>
+int chi2_launch(const fk_cov *c, const TO *O, const double *D, int R, double *out, TO *gO, Scratch &scr,
+                cudaStream_t s) {
+    double *zsq = out;
+    if (c->nblocks > 1) FK_CUDA(scr.get(&zsq, (size_t)c->nblocks * R));
+    const int ry = (R + RT - 1) / RT;
+    constexpr int YMAX = 65535;  // grid height limit: larger R runs in several launches
+    double *vg = nullptr;
+    size_t smem = (size_t)RT * c->maxn * sizeof(double);
+    if ((long long)RT * c->maxn > SMEM_VEC_DOUBLES) {
+        FK_CUDA(scr.get(&vg, (size_t)std::min(ry, YMAX) * c->nblocks * RT * c->maxn));
+        smem = 0;
+    }
+    for (int y0 = 0; y0 < ry; y0 += YMAX) {
+        const int gy = std::min(YMAX, ry - y0);
+        k_chi2_solve<TO, RT><<<dim3(c->nblocks, gy), SOLVE_THREADS, smem, s>>>(cview(c), O, D, R, y0 * RT, zsq,
+                                                                               gO, vg);
         count_launch();
         FK_CUDA(cudaGetLastError());
-        k_chi2_gred<TO><<<dim3(c->ntiles, rt), 256, 0, s>>>(cv, part, R, gO);
+    }
+    if (c->nblocks > 1) {
+        k_chi2_sum<<<(R + 127) / 128, 128, 0, s>>>(zsq, c->nblocks, R, out);
         count_launch();
         FK_CUDA(cudaGetLastError());
     }
     return FK_OK;
+}
+
+template <typename TO>
+int chi2_t(const fk_cov *c, const TO *O, const double *D, int R, double *out, TO *gO, cudaStream_t s) {
+    Scratch scr(s);
+    switch (pick_rt(c->maxn)) {
+        case 8: return chi2_launch<TO, 8>(c, O, D, R, out, gO, scr, s);
+        case 4: return chi2_launch<TO, 4>(c, O, D, R, out, gO, scr, s);
+        case 2: return chi2_launch<TO, 2>(c, O, D, R, out, gO, scr, s);
+    }
+    return chi2_launch<TO, 1>(c, O, D, R, out, gO, scr, s);
 }
 
 }  // namespace

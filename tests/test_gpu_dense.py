@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 ALL = ("fp64", "fp32", "bf16", "bf16x3", "tf32")
 # max |err| / S per mode: FP64/FP32 as the other parity tests; the tensor-core
 # modes as for Eq. 1 (two operand roundings of the mode plus FP32 sums)
-BOUND = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2 ** -7, "tf32": 2 ** -9, "bf16x3": 2 ** -13}
+BOUND = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2 ** -7, "tf32": 2 ** -9, "bf16x3": 2 ** -16}
 
 
 def _dt(prec):
@@ -53,6 +53,30 @@ def test_dense_exact_small_integers(shape):
     for prec in ALL:
         O = run_dense(tab, L, prec)
         assert np.array_equal(O, O_ref), (prec, np.abs(O - O_ref).max())
+
+
+@pytest.mark.parametrize("side", ["L", "FK"])
+@pytest.mark.parametrize("shape", [(5, 37, 3), (300, 1000, 130), (8, 4099, 1)])
+def test_dense_bf16x3_cross_terms_exact(side, shape):
+    """Split operands in the dense product: one side holds v = h + l (h = +-1,
+    +-2 and l = k 2^-10, |k| <= 3: hi = h and lo = l exactly), the other side
+    integers in -1..1, so hi*hi + hi*lo + lo*hi is the exact product and the
+    FP32 sums (multiples of 2^-10, below 2^14) are exact: bit-equal to the
+    oracle.  Plain BF16 drops the lo parts and differs."""
+    nd, K, R = shape
+    rng = np.random.default_rng(nd + K + R + len(side))
+
+    def split(shape_):
+        h = rng.integers(1, 3, shape_) * rng.choice([-1.0, 1.0], shape_)
+        return h + rng.integers(-3, 4, shape_) * 2.0 ** -10
+
+    ints = lambda shape_: rng.integers(-1, 2, shape_).astype(np.float64)  # noqa: E731
+    fkd = split((nd, K)) if side == "FK" else ints((nd, K))
+    L = split((R, K)) if side == "L" else ints((R, K))
+    O_ref, _ = oracle.dense(fkd, L)
+    tab = fk.Table.dense(fkd, precs=("bf16x3", "bf16"))
+    assert np.array_equal(run_dense(tab, L, "bf16x3"), O_ref)
+    assert not np.array_equal(run_dense(tab, L, "bf16"), O_ref)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -18,6 +18,8 @@ import paper_1909_10547_b300 as fk
 from paper_1909_10547_b300 import workloads as W
 from paper_1909_10547_b300.fitstep import GlobalFit
 
+from bounds import fit_chain_scales
+
 pytestmark = pytest.mark.gpu
 
 SEED = 77
@@ -70,9 +72,18 @@ def test_fit_step_gradient_matches_oracle_chain(small_global, pipelined):
     chi_ref, gF_ref = oracle_chain(g, cov, D, g.F)
     chi = fit.chi2.cpu().numpy()
     gF = fit.gF.cpu().numpy()
-    np.testing.assert_allclose(chi, chi_ref, rtol=1e-11)
-    scale = np.abs(gF_ref).max()
-    assert np.abs(gF - gF_ref).max() <= 1e-11 * scale
+    # 1e-12 of the componentwise scale of the whole chain (forward sums S,
+    # residual, both substitutions, adjoint: tests/bounds.py)
+    B_chi, B_gF = fit_chain_scales(g.tables, g.F, cov.blocks, D)
+    assert np.all(np.abs(chi - chi_ref) <= 1e-12 * B_chi)
+    assert np.all(np.abs(gF - gF_ref) <= 1e-12 * B_gF)
+    # and plain relative 1e-12: chi^2 per replica, the gradient against its
+    # largest entry
+    np.testing.assert_allclose(chi, chi_ref, rtol=1e-12)
+    assert np.abs(gF - gF_ref).max() <= 1e-12 * np.abs(gF_ref).max()
+    print(f"chi2 rel {np.abs(chi / chi_ref - 1).max():.2e}, err/scale {(np.abs(chi - chi_ref) / B_chi).max():.2e}; "
+          f"gF rel to max {np.abs(gF - gF_ref).max() / np.abs(gF_ref).max():.2e}, "
+          f"err/scale {(np.abs(gF - gF_ref) / np.where(B_gF > 0, B_gF, 1)).max():.2e}")
 
 
 def test_fit_step_gradient_finite_differences(small_global):

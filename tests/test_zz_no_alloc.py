@@ -3,11 +3,14 @@ allocate device memory while they run (their GPU memory belongs to another
 allocator or is capped, or they cannot afford an allocation in a tight loop).
 Its partial sums live in a static device array instead of per-call scratch.
 
-Checked through the C ABI against fk_had_conv on the same inputs, on two
-calls in a row (a streaming call, then a many-replica call on another table,
-so the second reuses the array the first left behind), within the tolerances
-of the other parity tests: 1e-12 (FP64) and 1e-5 (FP32) of the sum of
-|terms|.  This file is collected last so a failure here never hides others.
+Checked through the C ABI on three calls in a row (a streaming call with
+R = 1, then the many-replica kernel's 16-wide replica tile with R = 3, then
+its wide tile with R = 37 on another table, so each call reuses the array the
+previous one left behind): bit-equal to fk_had_conv on the same inputs (the
+launches and their summation order are the same), and within the tolerances
+of the other parity tests of the FP64 oracle: 1e-12 (FP64) and 1e-5 (FP32) of
+the sum of |terms|.  This file is collected last so a failure here never
+hides others.
 """
 import ctypes
 
@@ -35,7 +38,8 @@ def _call(name, tab, F, O, prec):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_noalloc_matches_fk_had_conv_on_two_calls(prec):
     dt = torch.float64 if prec == "fp64" else torch.float32
-    cases = [W.config1(R=1), W.config1(R=37, seed=99, ndata=150, nc=40, nx=25)]
+    cases = [W.config1(R=1), W.config1(R=3, seed=98, ndata=90, nc=30, nx=20),
+             W.config1(R=37, seed=99, ndata=150, nc=40, nx=25)]
     for t, F in cases:
         tab = fk.Table.from_workload(t, precs=(prec,))
         Fd = torch.tensor(F, dtype=dt, device="cuda")
@@ -44,8 +48,9 @@ def test_noalloc_matches_fk_had_conv_on_two_calls(prec):
         _call("fk_had_conv", tab, Fd, O_ref, prec)
         _call("fk_had_conv_noalloc", tab, Fd, O_new, prec)
         torch.cuda.synchronize()
-        _, S = oracle.had(t, F)
-        err = np.abs(O_new.double().cpu().numpy() - O_ref.double().cpu().numpy())
+        assert torch.equal(O_new, O_ref)
+        want, S = oracle.had(t, F)
+        err = np.abs(O_new.double().cpu().numpy() - want)
         assert np.all(err <= TOL[prec] * S), (err / S).max()
 
 

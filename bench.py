@@ -2,15 +2,24 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec P] [--impl ours|reference]
 
-A step is one pass of the whole hot path over the global-shaped fit set
+A fit step is one pass of the whole hot path over the global-shaped fit set
 (40 synthetic datasets, 12 DIS + 28 hadronic, ~4500 data points, R = 100
 replicas on a shared 50-point x grid): forward convolution of every table,
-FP64 chi^2 with its gradient, adjoint of every table into dchi2/dF.  The
-metric is datapoint*replicas per second (sum of ndata * R over the step,
-divided by the step time).  Tables are device resident; the timed region
+FP64 chi^2 with its gradient, adjoint of every table into dchi2/dF.  A bench
+step is --inner (default 10) consecutive fit steps, so that the timed region
+of the driver's step count lasts a quarter of a second or more.  The metric
+is datapoint*replicas per second (sum of ndata * R over the fit steps,
+divided by their time).  Tables are device resident; the timed region
 replays the step's CUDA graphs.  Under torchrun each rank runs its own copy
 of the workload (weak scaling, no collective on the data path); rank 0
 prints one JSON line.
+
+With one GPU the line also carries: `accuracy` (the fit step's chi^2 and
+gradient against the FP64 oracle, from the CPU-baseline leg's own run),
+`kernels` (kernel-level lines with their own rooflines: stress table R = 1
+streaming and R = 1000 tensor cores, configs 0-2, Table 3's R = 1 rows) and
+`serve` (a bounded run of the served mixed workload: 500 Poisson arrivals
+at 2000/s, p50/p99/max latency, saturation and per-request throughput).
 """
 import argparse
 import hashlib
@@ -40,19 +49,24 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner", type=int, default=10,
+                    help="fit case: fit steps per bench step (the timed region is steps x inner fit steps)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="fit case: skip the kernel-level lines and the served-mix block")
     ap.add_argument("--phases", action="store_true",
                     help="fit case: run the step as three separate phases (per-phase timing) "
                          "instead of the pipelined per-table chains")
     ap.add_argument("--waves", type=int, default=1, help="fit case: forward waves of the pipelined step")
     ap.add_argument("--streams", type=int, default=0,
                     help="fit case: streams the tables are spread over (0: one per table)")
-    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent", "dense"],
+    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent", "dense", "peaks"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
                          "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
                          "serve: the served mixed workload (Poisson arrivals over 41 resident tables); "
                          "descent: Adam on the PDF parameters of every replica, iterations of the fit; "
                          "dense: the paper's Table 3 product FK[ndata x 35721] . PDF[35721 x R] "
-                         "(--ndata, --replicas; default 2000 x 2000)")
+                         "(--ndata, --replicas; default 2000 x 2000); "
+                         "peaks: measures the TF32 (cuBLAS), FP32 and FP64 (multiply-add loops) peaks")
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
@@ -65,13 +79,44 @@ def parse():
 
 
 def peaks():
+    """HBM and BF16 peaks from MEASURED_PEAKS.json (driver-measured), plus the
+    TF32, FP32 and FP64 peaks this repository measured the same way
+    (profiles/peaks.txt, written from `bench.py --case peaks`)."""
     p = os.path.join(HERE, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             m = json.load(f)
-        return m, "measured"
-    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
-            "sm_max_mhz": 2032.0}, "fallback"
+        src = "measured"
+    else:
+        m = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}
+        src = "fallback"
+    try:
+        for ln in open(os.path.join(HERE, "profiles", "peaks.txt")):
+            w = ln.split()
+            if len(w) >= 2 and not ln.startswith("#") and w[0].endswith("_tflops"):
+                m[w[0]] = float(w[1])
+    except OSError:
+        pass
+    return m, src
+
+
+def peak_of(prec, pk, sustained=False):
+    """(TFLOP/s, source) of the arithmetic a mode runs on: the tensor pipe for
+    BF16 / BF16 hi+lo (BF16 peak) and TF32, the CUDA cores for FP32 and FP64."""
+    mhz = pk.get("sm_max_mhz", 2032.0)
+    if prec in ("bf16", "bf16x3"):
+        return (pk["bf16_tflops_sustained"] if sustained else pk["bf16_tflops"]), "measured (cuBLAS BF16)"
+    if prec == "tf32":
+        if "tf32_tflops" in pk:
+            return pk["tf32_tflops"], "measured (cuBLAS TF32, profiles/peaks.txt)"
+        return pk["bf16_tflops"] / 2.0, "BF16 measured / 2 (nominal ratio)"
+    if prec == "fp32":
+        if "fp32_tflops" in pk:
+            return pk["fp32_tflops"], "measured (FP32 FMA loop, profiles/peaks.txt)"
+        return 148 * 128 * 2 * mhz * 1e6 / 1e12, "derived: 148 SMs x 128 FMA/clock x max clock"
+    if "fp64_tflops" in pk:
+        return pk["fp64_tflops"], "measured (FP64 FMA loop, profiles/peaks.txt)"
+    return 148 * 2 * 2 * mhz * 1e6 / 1e12, "derived: 148 SMs x 2 FP64 FMA/clock x max clock"
 
 
 def dist_init(n):
@@ -250,25 +295,352 @@ class Clocks:
                 "samples": len(self.samples), "source": "nvml" if self.nv is not None else "nvidia-smi"}
 
 
-def cpu_baseline(g, replicas):
-    """The FP64 oracle (as it stands) on a bounded sample: the same fit step
-    for the first `replicas` replicas.  Returns (dp*rep/s, threads, seconds)."""
+def cpu_baseline(g, blocks, D_parts, replicas_all=16, replicas_one=1):
+    """The FP64 oracle (as it stands) on bounded samples of the same fit step
+    (same tables, covariance blocks and pseudo-data as the GPU run): the first
+    `replicas_all` replicas on all host cores (best of 5) and `replicas_one`
+    on one core (best of 3).  Also returns the oracle's chi^2 and dchi2/dF of
+    the all-core sample, which the accuracy block compares with the GPU."""
     import oracle
-    from paper_1909_10547_b300 import workloads as W
-    F = g.F[:replicas]
-    # set-up outside the timed region: covariance factors and pseudo-data
-    o_true = [oracle.conv(t, g.F_true)[0][0] for t in g.tables]
-    cov = W.covariance(o_true, SEED)
-    D = W.pseudo_data(o_true, SEED)
-    Ls = [oracle.cholesky(b) for b in cov.blocks]
-    t0 = time.perf_counter()
-    for t, L, d in zip(g.tables, Ls, D):
-        O, _ = oracle.conv(t, F)
-        _, gO = oracle.chi2(L, O, d)
-        oracle.conv_grad(t, F, gO)
-    dt = time.perf_counter() - t0
+    Ls = [oracle.cholesky(b) for b in blocks]
+
+    def run(F):
+        chi = np.zeros(F.shape[0])
+        gF = np.zeros_like(F)
+        for t, L, d in zip(g.tables, Ls, D_parts):
+            O, _ = oracle.conv(t, F)
+            c, gO = oracle.chi2(L, O, d)
+            chi += c
+            gF += oracle.conv_grad(t, F, gO)
+        return chi, gF
+
+    def best(F, n):
+        b = float("inf")
+        out = None
+        for _ in range(n):
+            t0 = time.perf_counter()
+            out = run(F)
+            b = min(b, time.perf_counter() - t0)
+        return b, out
+
     ntot = sum(t.ndata for t in g.tables)
-    return ntot * replicas / dt, oracle.threads(), dt
+    cores = oracle.threads()
+    t_all, (chi, gF) = best(g.F[:replicas_all], 5)
+    oracle.set_threads(1)
+    try:
+        t_one, _ = best(g.F[:replicas_one], 3)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": ntot * replicas_all / t_all, "cores": cores, "seconds": t_all, "replicas": replicas_all,
+            "value_1core": ntot * replicas_one / t_one, "seconds_1core": t_one, "replicas_1core": replicas_one,
+            "chi2": chi, "gF": gF}
+
+
+def time_calls(fn, steps, flush=None):
+    """Milliseconds per call of fn (one CUDA graph of it, replayed).  Warm:
+    `steps` replays back to back between two events.  With flush (a tensor
+    larger than L2): before every call flush is overwritten, then that call
+    alone is timed; the mean of the calls is returned."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    tot = 0.0
+    for _ in range(steps):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def roof_entry(prec, byts, flops, ms, kernel, traffic=None):
+    """Roofline of one timed call: HBM when flops/bytes is below the ridge of
+    the mode's peak, else the tensor pipe (reduced modes) or the CUDA cores."""
+    pk, src = peaks()
+    tpeak, psrc = peak_of(prec, pk)
+    ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
+    tc = prec in ("bf16", "bf16x3", "tf32")
+    if flops / byts < ridge:
+        ach = byts / (ms * 1e-3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+             "algorithmic_bytes": byts, "peak_source": src}
+    else:
+        ach = flops / (ms * 1e-3) / 1e12
+        r = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
+             "frac": ach / tpeak, "algorithmic_flops": flops, "peak_source": psrc}
+    r["traffic"] = traffic
+    r["kernel"] = kernel
+    return r
+
+
+def kernel_lines(args, stress_tab=None, stress_t=None):
+    """Kernel-level lines: each one call of one path, timed on its own with
+    its own roofline.  Stress table (2000 x 196 channels x 50 x 50; resident
+    tables far larger than L2): R = 1 FP32 streaming and R = 1000 BF16 on the
+    tensor cores.  Configs 1-2 table (200 x 60 x 30 x 30, 43 MB in FP32: it
+    fits in L2, so each line is given warm, back to back, and cold, L2 flushed
+    by a 256 MB write before every call).  Config 0 (DIS, 64 x 9 x 40, FP64,
+    R = 1): one call's latency, and 4096 such tables stacked into one table
+    (262144 data points, 755 MB) for bandwidth.  Table 3's R = 1 rows with
+    K = 10^6 and 10^7 (ndata = 8, FP32 streaming of the dense table)."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    out = []
+    steps = max(args.steps, 20)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def line(name, prec, units, ms, roof, **extra):
+        d = {"name": name, "prec": prec, "value": units / (ms * 1e-3), "unit": UNIT, "ms": ms,
+             "roofline": roof}
+        d.update(extra)
+        out.append(d)
+
+    # stress table
+    if stress_tab is not None:
+        nd = stress_t.ndata
+        elems = stress_t.fk.size
+        F1 = torch.tensor(W.pdf_replicas(W.xgrid(50, 1e-7), W.pdf_params(np.random.default_rng(1)), 1, None),
+                          dtype=torch.float32, device="cuda")
+        O1 = torch.empty((1, nd), dtype=torch.float32, device="cuda")
+        ms = time_calls(lambda: fk.conv(stress_tab, F1, "fp32", out=O1), steps)
+        line("stress table 2000x196x50x50, R=1, FP32 streaming", "fp32", nd, ms,
+             roof_entry("fp32", elems * 4, 2.0 * elems, ms, "k_stream",
+                        traffic_of("k_stream", "fp32", nd, 1)))
+        R = 1000
+        FR = torch.tensor(W.pdf_replicas(W.xgrid(50, 1e-7), W.pdf_params(np.random.default_rng(1)), R,
+                                         np.random.default_rng(2)), dtype=torch.float32, device="cuda")
+        OR = torch.empty((R, nd), dtype=torch.float32, device="cuda")
+        for prec in ("bf16", "bf16x3"):
+            ms = time_calls(lambda: fk.conv(stress_tab, FR, prec, out=OR), max(5, steps // 4))
+            line(f"stress table, R=1000, {prec} tensor cores", prec, nd * R, ms,
+                 roof_entry(prec, elems * ESZ[prec], 2.0 * elems * R, ms,
+                            "k_tc (whole call: operand packing + tcgen05 kernel)", traffic_of("k_tc", prec, nd, R)))
+        del FR, OR
+    # configs 1-2 table
+    t1, F1h = W.config1(R=512)
+    tab1 = fk.Table.from_workload(t1, precs=("fp32", "bf16", "bf16x3", "tf32"))
+    e1 = t1.fk.size
+    nd1 = t1.ndata
+    Fa = torch.tensor(F1h, dtype=torch.float32, device="cuda")
+    Oa = torch.empty((512, nd1), dtype=torch.float32, device="cuda")
+    Fs = Fa[:1].contiguous()
+    Os = torch.empty((1, nd1), dtype=torch.float32, device="cuda")
+    for cold in (False, True):
+        ms = time_calls(lambda: fk.conv(tab1, Fs, "fp32", out=Os), steps, flush if cold else None)
+        line(f"config 1 table 200x60x30x30, R=1, FP32 streaming, {'cold L2' if cold else 'warm L2'}", "fp32", nd1,
+             ms, roof_entry("fp32", e1 * 4, 2.0 * e1, ms, "k_stream"))
+    for prec in ("bf16", "tf32", "bf16x3"):
+        for cold in (False, True):
+            ms = time_calls(lambda: fk.conv(tab1, Fa, prec, out=Oa), steps, flush if cold else None)
+            line(f"config 2: config 1 table, R=512, {prec} tensor cores, {'cold L2' if cold else 'warm L2'}", prec,
+                 nd1 * 512, ms, roof_entry(prec, e1 * ESZ[prec], 2.0 * e1 * 512, ms,
+                                           "k_tc (whole call: operand packing + tcgen05 kernel)"))
+    del tab1
+    # config 0 (DIS, FP64, R = 1) and 4096 of its tables stacked
+    t0, F0h = W.config0()
+    tab0 = fk.Table.from_workload(t0, precs=("fp64",))
+    F0 = torch.tensor(F0h, device="cuda")
+    O0 = torch.empty((1, t0.ndata), dtype=torch.float64, device="cuda")
+    used0 = t0.ndata * len(t0.flav) * t0.nx
+    for cold in (False, True):
+        ms = time_calls(lambda: fk.dis_conv(tab0, F0, "fp64", out=O0), steps, flush if cold else None)
+        line(f"config 0: DIS 64x9x40, R=1, FP64, one call ({'cold L2' if cold else 'warm L2'})", "fp64", t0.ndata, ms,
+             roof_entry("fp64", used0 * 8, 2.0 * used0, ms, "k_stream<DIS> + k_reduce_parts"),
+             latency_us=ms * 1e3)
+    del tab0
+    nb = 4096
+    rng = np.random.default_rng(10547)
+    big = np.abs(rng.standard_normal((nb * t0.ndata, len(t0.flav), t0.nx))) * (W.xgrid(t0.nx, 1e-7) ** 0.3)[None, None, :]
+    tabb = fk.Table.dis(big, t0.flav, None, t0.nx, precs=("fp64",))
+    del big
+    Ob = torch.empty((1, nb * t0.ndata), dtype=torch.float64, device="cuda")
+    ms = time_calls(lambda: fk.dis_conv(tabb, F0, "fp64", out=Ob), steps)
+    ub = used0 * nb
+    line("config 0 x 4096: 4096 DIS tables 64x9x40 stacked (262144 points), R=1, FP64", "fp64", nb * t0.ndata, ms,
+         roof_entry("fp64", ub * 8, 2.0 * ub, ms, "k_stream<DIS> + k_reduce_parts"))
+    del tabb
+    # Table 3 rows with R = 1: ndata = 8, K = 1e6, 1e7
+    for K in (10 ** 6, 10 ** 7):
+        fkd = np.random.default_rng(K).standard_normal((8, K))
+        tabd = fk.Table.dense(fkd, precs=("fp32",))
+        del fkd
+        L = torch.rand((1, K), dtype=torch.float32, device="cuda")
+        Od = torch.empty((1, 8), dtype=torch.float32, device="cuda")
+        ms = time_calls(lambda: fk.dense_conv(tabd, L, "fp32", out=Od), steps, flush if 8 * K * 4 < 126e6 else None)
+        line(f"Table 3 row: dense 8 x {K:.0e} . PDF [{K:.0e} x 1], FP32 streaming", "fp32", 8, ms,
+             roof_entry("fp32", 8 * K * 4 + K * 4, 2.0 * 8 * K, ms, "k_stream<DENSE> + k_reduce_parts"),
+             paper_seconds={10 ** 6: 5.0e-3, 10 ** 7: 5.7e-2}[K])
+        del tabd, L
+    return out
+
+
+def serve_block(args, g, tabs, tprec, stress_tab=None, n=500, rate=2000.0):
+    """The served mixed workload, bounded: n requests with Poisson arrivals at
+    `rate` over the global-set tables (+ the stress table), R from
+    {1, 10, 100, 1000}, resident tables, 150 GB budget.  Reports open-loop
+    p50/p99/max latency (submit to the poll that sees the result), the
+    saturation throughput (closed loop, 64 in flight) and the same requests
+    one at a time through the plain per-request path (H2D, conv, D2H)."""
+    import threading
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    alltabs = list(tabs) + ([stress_tab] if stress_tab is not None else [])
+    allprec = list(tprec) + ([args.prec] if stress_tab is not None else [])
+    nxg = [t.nxg for t in alltabs]
+    srv = fk.Server(budget_bytes=150 << 30, max_inflight=8)
+    ids = [srv.add_table(t) for t in alltabs]
+    rng = np.random.default_rng(SEED + 1)
+    which = rng.integers(0, len(alltabs), n)
+    Rs = rng.choice(W.REPLICA_CHOICES, n)
+    arr = W.arrivals(rng, rate, n)
+    pool = {}
+    for k in range(n):
+        key = (nxg[which[k]], int(Rs[k]), allprec[which[k]])
+        if key not in pool:
+            x = g.x if key[0] == 50 else W.xgrid(key[0], 1e-7)
+            F = W.pdf_replicas(x, g.params, key[1], np.random.default_rng(key[1]))
+            pool[key] = F.astype(np.float64 if key[2] == "fp64" else np.float32)
+    work = [(int(which[k]), pool[(nxg[which[k]], int(Rs[k]), allprec[which[k]])], allprec[which[k]])
+            for k in range(n)]
+    units = sum(alltabs[w].ndata * F.shape[0] for w, F, _ in work)
+    for k in range(len(alltabs)):  # warm-up: every table once
+        key = next(kk for kk in pool if kk[0] == nxg[k] and kk[2] == allprec[k])
+        srv.wait(srv.submit(ids[k], pool[key], allprec[k]), 600000)
+    tickets = [None] * n
+    t_sub = np.zeros(n)
+    t_done = np.zeros(n)
+
+    def poller():
+        outstanding = set()
+        nxt = 0
+        while nxt < n or outstanding:
+            while nxt < n and tickets[nxt] is not None:
+                outstanding.add(nxt)
+                nxt += 1
+            for k in list(outstanding):
+                ok, _ = srv.poll(tickets[k])
+                if ok:
+                    t_done[k] = time.perf_counter()
+                    outstanding.discard(k)
+            time.sleep(0.0001)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for k, (w, F, p) in enumerate(work):
+        delay = t0 + arr[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        t_sub[k] = time.perf_counter()
+        tickets[k] = srv.submit(ids[w], F, p)
+    th.join()
+    lat = (t_done - t_sub) * 1e3
+    span = t_done.max() - t_sub.min()
+    s0 = time.perf_counter()
+    inflight = []
+    for w, F, p in work:
+        if len(inflight) >= 64:
+            srv.wait(inflight.pop(0), 600000)
+        inflight.append(srv.submit(ids[w], F, p))
+    for tk in inflight:
+        srv.wait(tk, 600000)
+    sat = time.perf_counter() - s0
+    st = srv.stats()
+    srv.close()
+    t1 = time.perf_counter()
+    plain = []
+    for w, F, p in work:
+        a = time.perf_counter()
+        Fd = torch.from_numpy(F).to("cuda")
+        fk.conv(alltabs[w], Fd, p).cpu()
+        plain.append((time.perf_counter() - a) * 1e3)
+    plain_span = time.perf_counter() - t1
+    return {"requests": n, "offered_rate": rate, "tables": len(alltabs),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "achieved_rate": n / span, "open_loop_value": units / span,
+            "saturation_value": units / sat, "unit": UNIT, "launches": st["launches"],
+            "per_request": {"value": units / plain_span, "p50_ms": float(np.percentile(plain, 50)),
+                            "p99_ms": float(np.percentile(plain, 99)),
+                            "what": "one request at a time: H2D, fk conv, D2H, synchronise"}}
+
+
+def run_peaks(args):
+    """TF32 tensor-core peak by the MEASURED_PEAKS method (cuBLAS 8192^3 GEMM
+    through torch, best of 10 and back to back for 4 s), and the FP32 / FP64
+    CUDA-core multiply-add rates with fk_fma_probe (8 chains per thread, one
+    wave of 8 CTAs of 256 threads per SM, best of 10 and 4 s back to back).
+    The clock is sampled throughout."""
+    import ctypes
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import _lib
+    res = {}
+    torch.backends.cuda.matmul.allow_tf32 = True
+    a = torch.randn(8192, 8192, device="cuda")
+    b = torch.randn(8192, 8192, device="cuda")
+    c = torch.empty(8192, 8192, device="cuda")
+
+    def rate(fn, flops):
+        fn()
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        n = 0
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        while time.perf_counter() - t0 < 4.0:
+            fn()
+            n += 1
+            if n % 8 == 0:
+                torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        return best, flops * n / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    with Clocks(torch.cuda.current_device()) as clk:
+        res["tf32_tflops"], res["tf32_tflops_sustained"] = rate(lambda: torch.matmul(a, b, out=c), 2.0 * 8192 ** 3)
+        del a, b, c
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        blocks = 8 * sms
+        lib = _lib.load()
+        for name, prec, dt, iters in (("fp32", _lib.FK_FP32, torch.float32, 1 << 16),
+                                      ("fp64", _lib.FK_FP64, torch.float64, 1 << 11)):
+            sink = torch.zeros(blocks, dtype=dt, device="cuda")
+            stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            fl = 2.0 * 8 * iters * 256 * blocks
+            res[f"{name}_tflops"], res[f"{name}_tflops_sustained"] = rate(
+                lambda: lib.fk_fma_probe(prec, blocks, iters, ctypes.c_void_p(sink.data_ptr()), stream), fl)
+    res["clocks"] = clk.summary()
+    res["how"] = ("TF32: torch.matmul fp32 8192^3 with TF32 allowed (cuBLAS), 2 N^3 flops; FP32 / FP64: "
+                  "fk_fma_probe, 8 independent FMA chains per thread, 8 x SMs CTAs of 256 threads; best of 10 "
+                  "(burst) and back to back for 4 s (sustained), CUDA events")
+    print(json.dumps(res), flush=True)
 
 
 def run_reference(args, rank, world, dist):
@@ -323,8 +695,8 @@ def roofline(fit, seg, prec):
     modes: FP32).  Algorithmic flops: 2 per multiply-add of the definition.
     The bound is HBM when flops/bytes is below the ridge of the measured
     peaks, else the tensor pipe (reduced modes) or the ALUs (FP32 / FP64 on
-    the CUDA cores).  The FP64 chi^2 phase is ALU-bound: peak 148 SMs x 2
-    FP64 FMA/clock x 2 flop x 2032 MHz = 1.203 TFLOP/s."""
+    the CUDA cores).  The FP64 chi^2 phase is bound by the FP64 multiply-add
+    rate (peak_of: measured with fk_fma_probe when profiles/peaks.txt has it)."""
     pk, src = peaks()
     dom = max(seg, key=seg.get)
     t = seg[dom] * 1e-3
@@ -341,19 +713,14 @@ def roofline(fit, seg, prec):
                 "algorithmic_bytes": byts, "algorithmic_flops": flops, "peak_source": src}
     flops = fit.flops[dom]
     if dom == "loss":
-        peak = 148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        peak, psrc = peak_of("fp64", pk)
         return {"bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "frac": flops / t / 1e12 / peak, "traffic": None, "kernel": "loss phase (FP64 chi^2)",
-                "peak_source": "derived from unit counts and max clock", "phase_ms": seg}
+                "peak_source": psrc, "phase_ms": seg}
     had_b = fit.elems["had"] * ESZ[prec]
     dis_b = fit.elems["dis"] * ESZ["fp32" if tc else prec]
     byts = had_b + dis_b
-    if tc:
-        tpeak = pk["bf16_tflops_sustained"] / (2.0 if prec == "tf32" else 1.0)
-    elif prec == "fp32":
-        tpeak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    else:
-        tpeak = 148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    tpeak, _ = peak_of(prec, pk, sustained=True)
     ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
     if flops / byts < ridge:
         ach = byts / t / 1e9
@@ -468,9 +835,7 @@ def run_dense(args):
     byts = nd * K * ESZ[prec]
     pk, src = peaks()
     tc = prec in ("bf16", "bf16x3", "tf32")
-    tpeak = (pk["bf16_tflops"] / (2.0 if prec == "tf32" else 1.0) if tc else
-             148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12 if prec == "fp32" else
-             148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12)
+    tpeak, _ = peak_of(prec, pk)
     ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
     kern = "k_tc" if tc else ("k_stream" if R <= 4 else "k_tile")
     if flops / byts < ridge:
@@ -546,9 +911,7 @@ def run_stress(args):
     flops = 2.0 * elems * R
     pk, src = peaks()
     tc = args.prec in ("bf16", "bf16x3", "tf32")
-    tpeak = (pk["bf16_tflops"] / (2.0 if args.prec == "tf32" else 1.0) if tc else
-             148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12 if args.prec == "fp32" else
-             148 * 2 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12)
+    tpeak, _ = peak_of(args.prec, pk)
     ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
     if flops / byts < ridge:
         ach = byts / (ms * 1e-3) / 1e9
@@ -766,6 +1129,9 @@ def main():
     if args.case == "dense":
         run_dense(args)
         return
+    if args.case == "peaks":
+        run_peaks(args)
+        return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world, dist)
@@ -791,11 +1157,14 @@ def main():
     launches = fit.launches_per_step()
     stream = torch.cuda.current_stream()
 
-    for _ in range(max(3, args.warmup)):
+    inner = max(1, args.inner)
+    for _ in range(max(3, args.warmup) * inner):
         fit.step()
     torch.cuda.synchronize()
     names = list(fit.graphs)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    # a bench step is `inner` consecutive fit steps: events between the
+    # graphs of the first fit step of each bench step give the per-graph split
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 2)] for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -807,6 +1176,9 @@ def main():
             for i, n in enumerate(names):
                 fit.graphs[n].replay()
                 ev[k][i + 1].record(stream)
+            for _ in range(inner - 1):
+                fit.step()
+            ev[k][-1].record(stream)
         torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
     if dist is not None:
@@ -815,8 +1187,11 @@ def main():
            for i, n in enumerate(names)}
     ms = sum(ev[k][0].elapsed_time(ev[k][-1]) for k in range(args.steps)) / args.steps
     ms = max_over_ranks(dist, ms)
+    fit_ms = ms / inner
+    if len(names) == 1:
+        seg = {names[0]: fit_ms}  # the pipelined step: the mean over all timed fit steps
 
-    # end to end: pinned host F in, chi2 and gF out, through the same calls
+    # end to end: per fit step, pinned host F in, chi2 and gF out, through the same calls
     F_host = torch.tensor(g.F, dtype=fit.io).pin_memory()
     chi2_host = torch.empty(fit.R, dtype=torch.float64).pin_memory()
     gF_host = torch.empty(fit.gF.shape, dtype=fit.io).pin_memory()
@@ -828,7 +1203,7 @@ def main():
         gF_host.copy_(fit.gF, non_blocking=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(args.steps * inner):
         fit.F.copy_(F_host, non_blocking=True)
         fit.step()
         chi2_host.copy_(fit.chi2, non_blocking=True)
@@ -837,11 +1212,12 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
 
-    units = fit.ntot * fit.R
+    units = fit.ntot * fit.R * inner
     value = job_throughput(units, world, ms)
     roof = roofline(fit, seg, args.prec)
-    if "step" in seg:
-        roof["traffic"] = traffic_of("fit_step", args.prec, fit.ntot, fit.R)
+    roof["traffic"] = None
+    roof["traffic_note"] = ("whole-step DRAM counters are not captured (one kernel at a time on small cases "
+                            "only); per-kernel traffic is in the kernels block")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -849,16 +1225,44 @@ def main():
                                            "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
             "data": "synthetic",
             "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
-                                               schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves"),
+                           schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves",
+                           fit_steps_per_step=inner, ms_per_fit_step=fit_ms),
             "roofline": roof,
             "e2e": {"value": job_throughput(units, world, ms_e2e), "unit": UNIT,
-                    "h2d_bytes_per_step": F_host.numel() * F_host.element_size(),
-                    "d2h_bytes_per_step": chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size()},
-            "gpu_launches": launches * args.steps, "clocks": clk.summary()}
+                    "h2d_bytes_per_step": inner * F_host.numel() * F_host.element_size(),
+                    "d2h_bytes_per_step": inner * (chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size())},
+            "gpu_launches": launches * args.steps * inner, "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, dt = cpu_baseline(g, 32)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"32 of {REPLICAS} replicas, whole fit step, {dt:.1f} s"}
+        D_parts = np.split(D, np.cumsum([t.ndata for t in g.tables])[:-1])
+        cb = cpu_baseline(g, cov.blocks, D_parts)
+        nr = cb["replicas"]
+        line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"{nr} of {REPLICAS} replicas, whole fit step (all 40 tables), FP64, "
+                                          f"best of 5: {cb['seconds']:.2f} s",
+                                "value_1core": cb["value_1core"],
+                                "sample_1core": f"{cb['replicas_1core']} replica, one core, best of 3: "
+                                                f"{cb['seconds_1core']:.2f} s"}
+        fit.F.copy_(torch.tensor(g.F, dtype=fit.io))
+        fit.step()
+        torch.cuda.synchronize()
+        chi = fit.chi2[:nr].cpu().numpy()
+        gF = fit.gF[:nr].double().cpu().numpy()
+        line["accuracy"] = {"reference": "FP64 oracle, same tables, covariance and pseudo-data",
+                            "replicas_compared": nr, "mode": args.prec,
+                            "chi2_max_rel_err": float(np.max(np.abs(chi / cb["chi2"] - 1))),
+                            "grad_max_err_rel_to_max": float(np.abs(gF - cb["gF"]).max() / np.abs(cb["gF"]).max())}
+    if rank == 0 and world == 1 and not args.no_extras:
+        from paper_1909_10547_b300 import workloads as W
+        try:
+            st = W.stress_table()
+            stress_tab = fk.Table.from_workload(st, precs=("fp32", "bf16", "bf16x3"))
+            line["kernels"] = kernel_lines(args, stress_tab, st)
+            del st
+            torch.cuda.synchronize()
+            line["serve"] = serve_block(args, g, fit.tabs, fit.tprec, stress_tab)
+            del stress_tab
+        except Exception as exc:  # the headline stands; say what failed
+            line["extras_error"] = f"{type(exc).__name__}: {exc}"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

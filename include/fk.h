@@ -327,6 +327,20 @@ int fk_pdf_grad(const void *F, const void *gF, int R, const double *x_grid, int 
 int fk_adam_step(void *p, const void *g, void *m, void *v, long long n, int t, double lr, double b1,
                  double b2, double eps, int prec, fk_stream stream);
 
+/* ------------------------------------------------------------ measurement */
+
+/*
+ * Arithmetic-rate probe (no counterpart in the paper: it measures the FP32 and
+ * FP64 multiply-add rates of the CUDA cores that the library's CUDA-core
+ * kernels are compared against).  Launches `blocks` CTAs of 256 threads; each
+ * thread runs 8 independent chains of `iters` fused multiply-adds in the
+ * precision prec (FK_FP32 or FK_FP64), i.e. 2 * 8 * iters * 256 * blocks
+ * flops.  sink: DEVICE, `blocks` elements of that type, never written in
+ * practice (it keeps the chains from being optimised away).  Asynchronous on
+ * stream.  Errors: FK_EINVAL, FK_ECUDA.
+ */
+int fk_fma_probe(int prec, int blocks, int iters, void *sink, fk_stream stream);
+
 /* -------------------------------------------------------------- serving */
 
 /*

@@ -41,10 +41,11 @@ def lib():
         L.fk_oracle_dense.argtypes = [I, ctypes.c_longlong, P, I, P, P, P]
         L.fk_oracle_cholesky.argtypes = [I, P, P]
         L.fk_oracle_chi2.argtypes = [I, P, I, P, P, P, P]
+        L.fk_oracle_set_threads.argtypes = [I]
         for f in (L.fk_oracle_dis, L.fk_oracle_had, L.fk_oracle_dis_grad,
                   L.fk_oracle_had_grad, L.fk_oracle_luminosity, L.fk_oracle_dense,
                   L.fk_oracle_cholesky, L.fk_oracle_chi2,
-                  L.fk_oracle_threads):
+                  L.fk_oracle_threads, L.fk_oracle_set_threads):
             f.restype = I
         _lib = L
     return _lib
@@ -52,6 +53,11 @@ def lib():
 
 def threads() -> int:
     return lib().fk_oracle_threads()
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of later calls (timing only); returns the count in effect."""
+    return lib().fk_oracle_set_threads(int(n))
 
 
 def _f64(a):

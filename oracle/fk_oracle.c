@@ -305,3 +305,15 @@ int fk_oracle_threads(void)
     return 1;
 #endif
 }
+
+/* Sets the OpenMP thread count of later calls (n >= 1); returns the count in
+ * effect afterwards.  Timing only: results do not depend on it (each output
+ * is computed by one thread in a fixed order). */
+int fk_oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#endif
+    return fk_oracle_threads();
+}

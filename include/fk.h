@@ -143,7 +143,11 @@ int fk_table_info(const fk_table *t, int *kind, int *ndata, int *nchannels, int 
 /* ---------------------------------------------------------- convolution */
 
 /*
- * DIS observables of table t (kind DIS) for R >= 1 replicas.
+ * DIS observables of table t (kind DIS) for R >= 1 replicas.  FP64 and FP32
+ * run on the CUDA cores; the reduced modes run the plain product
+ * O[r][d] = sum_{(k,i)} FK[d][(k,i)] F[r][flav[k]][xmap[i]] on the tensor
+ * cores (M = replicas, N = data points, K = active flavours x points, never
+ * split, so a replica's result does not depend on R).
  * F: DEVICE [R][14][nx_grid] (double for FK_FP64, float otherwise).
  * O: DEVICE, same type, replica r's ndata values at O + r * ldo (ldo = 0
  *    means ldo = ndata, i.e. a dense [R][ndata] array); overwritten.  A
@@ -234,12 +238,13 @@ int fk_had_conv_noalloc(const fk_table *t, const void *F, int R, void *O, int ld
  * otherwise).  accumulate = 0 overwrites all of gF (grid points the table does
  * not use are set to 0); accumulate = 1 adds into gF, so the gradients of
  * several tables sharing one grid can be summed in call order.  F is not read
- * for DIS tables (may be NULL).  The reduced modes (hadronic tables) run on
- * the tensor cores with the forward's operand rounding: the products of the
+ * for DIS tables (may be NULL).  The reduced modes run on the tensor cores
+ * with the forward's operand rounding.  Hadronic tables: the products of the
  * table with the PDF of one flavour go through the MMA in the mode's type with
  * FP32 accumulation, and gO and the remaining PDF factor are applied in FP32.
- * Like the forward, they are offered for hadronic tables only.  Dense tables
- * have no adjoint here (FK_EUNSUPPORTED).
+ * DIS tables: the product gO FK (K = data points) goes through the MMA with gO
+ * rounded to the mode, then is scattered onto the grid.  Dense tables have no
+ * adjoint here (FK_EUNSUPPORTED).
  */
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
                      void *gF, int accumulate, int prec, fk_stream stream);

@@ -133,8 +133,6 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
         if (xinv[xm[i]] >= 0) return fail(FK_EINVAL, "xmap entries must be distinct");
         xinv[xm[i]] = i;
     }
-    if (kind == FK_KIND_DIS && (mask & TC_PRECS))
-        return fail(FK_EUNSUPPORTED, "DIS tables offer FP64 and FP32 only");
 
     keep_pool();
     fk_table *t = new fk_table();
@@ -161,7 +159,7 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
         return rc;
     }
     if (mask & TC_PRECS) {
-        rc = tc_build(t, fk);
+        rc = kind == FK_KIND_HAD ? tc_build(t, fk) : tc_build_dis(t, fk);
         if (rc) {
             table_free(t);
             return rc;
@@ -274,7 +272,10 @@ int fk_dis_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
                 fk_stream stream) {
     int rc = check_conv(t, FK_KIND_DIS, F, R, O, ldo, prec);
     if (rc) return rc;
-    return fwd_cc(t, F, R, O, ldo ? ldo : t->ndata, prec == FK_FP64, (cudaStream_t)stream);
+    ldo = ldo ? ldo : t->ndata;
+    if (prec == FK_FP64 || prec == FK_FP32)
+        return fwd_cc(t, F, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    return dis_tc(t, (const float *)F, R, (float *)O, ldo, prec, (cudaStream_t)stream);
 }
 
 int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int prec,
@@ -320,9 +321,13 @@ int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo,
     if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
     const bool f64 = prec == FK_FP64;
     ldgo = ldgo ? ldgo : t->ndata;
-    if (prec != FK_FP64 && prec != FK_FP32)  // tensor-core modes (hadronic tables only)
+    if (prec != FK_FP64 && prec != FK_FP32) {  // tensor-core modes
+        if (t->kind == FK_KIND_DIS)
+            return dis_bwd_tc(t, (const float *)gO, ldgo, R, (float *)gF, accumulate ? 1 : 0, prec,
+                              (cudaStream_t)stream);
         return bwd_tc(t, (const float *)F, (const float *)gO, ldgo, R, (float *)gF, accumulate ? 1 : 0,
                       prec, (cudaStream_t)stream);
+    }
     return bwd_cc(t, F, gO, ldgo, R, gF, accumulate ? 1 : 0, f64, (cudaStream_t)stream);
 }
 

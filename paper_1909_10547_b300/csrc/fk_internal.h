@@ -70,6 +70,8 @@ struct TcGroups {
 //    n = j * G + d % G holds x_j, K runs over (channel, x_i).
 struct TcPack {
     TcGroups grp{};
+    int n_rows = 0;     // B rows per tile (MMA N)
+    int ntile_n = 0;    // B tiles
     int ktot = 0;       // used K (sum of padded group lengths)
     int ktot_pad = 0;   // row length: whole pipeline stages (a multiple of 64 or 128)
     __nv_bfloat16 *hi = nullptr;  // BF16 / hi part
@@ -145,6 +147,12 @@ int tc_build(fk_table *t, const double *host_fk);
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
 int tc_build_dense(fk_table *t, const double *host_fk);
 int dense_tc(const fk_table *t, const float *L, int R, float *O, int ldo, int prec, cudaStream_t s);
+// DIS tables on the tensor cores: the forward is the plain product
+// FK[d][(k,i)] F[r][(a_k, x_i)], the adjoint the product of gO with FK^T
+int tc_build_dis(fk_table *t, const double *host_fk);
+int dis_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
+int dis_bwd_tc(const fk_table *t, const float *gO, int ldgo, int R, float *gF, int accumulate, int prec,
+               cudaStream_t s);
 int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
            int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);

@@ -1085,7 +1085,7 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
     if (p.nrt % 2 == 0) {
         p.pwait = tc_pwait(p, tc_stages<PREC, 2>(), Tr<PREC>::KCS);
         auto kern = k_tc<PREC, G, MODE, 2>;
-        const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(t->tc.n_rows));
+        const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(p.n_rows));
         // opt in once at the largest tile (n_rows = 256) so that every table fits
         int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 2>(256));
         if (rc) return rc;
@@ -1113,7 +1113,7 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
     int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;
     const int grid = std::min(p.ntiles, sm_count());
-    kern<<<grid, TC_THREADS, one_per_sm(tc_smem_bytes<PREC, 1>(t->tc.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
+    kern<<<grid, TC_THREADS, one_per_sm(tc_smem_bytes<PREC, 1>(p.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
@@ -1139,8 +1139,7 @@ int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2
 // packing of the table, builds its tensor maps and fills the common params.
 template <int PREC>
 int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch &scr, float *Fm,
-            cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p) {
-    const TcLayout &L = t->tc;
+            cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p, int frow_in = -1) {
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float *f32 = nullptr;
@@ -1152,7 +1151,8 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
         if (PREC == FK_BF16X3) FK_CUDA(scr.get(&lo, nA));
     }
     // A rows: the PDF grid of a replica, or a dense table's PDF matrix row
-    const int frow = t->kind == FK_KIND_DENSE ? (int)t->E : NFL * t->nxg;
+    // (or, when given, rows of frow_in elements: the adjoint's gO)
+    const int frow = frow_in >= 0 ? frow_in : t->kind == FK_KIND_DENSE ? (int)t->E : NFL * t->nxg;
     k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
                        s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
     count_launch();
@@ -1170,15 +1170,15 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     if (PREC != FK_BF16X3) mA2 = mA;
     p = TcParams{};
     p.nrt = R_pad / TC_M;
-    p.ntiles = L.ntile_n * p.nrt;
-    p.ntile_n = L.ntile_n;
+    p.ntiles = pk.ntile_n * p.nrt;
+    p.ntile_n = pk.ntile_n;
     p.nsplit = 1;
     p.nchunks = pk.ktot_pad / Tr<PREC>::KCS;
-    p.n_rows = L.n_rows;
+    p.n_rows = pk.n_rows;
     // narrow tiles (G * nx <= 128, i.e. nx <= 8) keep four accumulators of 128
     // TMEM columns in flight instead of two of 256, so the short channel
     // groups of such tables wait less on the epilogue
-    p.nbl = L.n_rows <= 128 ? 2 : 1;
+    p.nbl = pk.n_rows <= 128 ? 2 : 1;
     p.ngroups = pk.grp.ngroups;
     p.nx = t->nx;
     p.ndata = t->ndata;
@@ -1371,6 +1371,8 @@ int tc_build(fk_table *t, const double *host_fk) {
         }
     L.n_rows = (L.G * t->nx + 15) / 16 * 16;
     L.ntile_n = (t->ndata + L.G - 1) / L.G;
+    L.fwd.n_rows = L.bwd.n_rows = L.n_rows;
+    L.fwd.ntile_n = L.bwd.ntile_n = L.ntile_n;
     const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
     const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
     const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
@@ -1449,29 +1451,16 @@ int tc_build(fk_table *t, const double *host_fk) {
     return FK_OK;
 }
 
-// Tensor-core layout of a dense table (the paper's Table 3 product): tiles of
-// n_rows = min(256, ndata rounded up to 16) data points, one group spanning
-// K, the A operand gathered from the caller's PDF matrix through the identity
-// map.
-template <int PREC>
-int pack_dense(fk_table *t, const double *d_fk, cudaStream_t s) {
-    const TcLayout &L = t->tc;
-    const TcPack &pk = L.fwd;
-    const long long rows = (long long)L.ntile_n * L.n_rows;
-    const unsigned blocks = (unsigned)std::min<long long>((rows * pk.ktot_pad + 255) / 256, 148LL * 32);
-    k_pack_dense<PREC><<<blocks, 256, 0, s>>>(d_fk, t->ndata, t->E, rows, pk.ktot_pad, pk.hi, pk.lo, pk.f32);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    return FK_OK;
-}
+namespace {
 
-int tc_build_dense(fk_table *t, const double *host_fk) {
-    TcLayout &L = t->tc;
-    TcPack &pk = L.fwd;
-    const long long K = t->E;
-    L.G = 16;  // not used by the dense epilogue
-    L.n_rows = std::min(256, (t->ndata + 15) / 16 * 16);
-    L.ntile_n = (t->ndata + L.n_rows - 1) / L.n_rows;
+// Plain products on the tensor cores (the dense tables of the paper's Table
+// 3 and the DIS tables): the B operand is a row-major FP64 matrix [nrows][K]
+// packed into tiles of n_rows = min(256, nrows rounded up to 16) rows, one
+// group spanning K; the A operand is gathered through km (K entries; -1 for
+// none), from a dense table's PDF matrix, a DIS replica's PDF grid or gO.
+int plain_layout(fk_table *t, TcPack &pk, int nrows, long long K, const std::vector<int> &km_in) {
+    pk.n_rows = std::min(256, (nrows + 15) / 16 * 16);
+    pk.ntile_n = (nrows + pk.n_rows - 1) / pk.n_rows;
     pk.grp = TcGroups{};
     pk.grp.ngroups = 1;
     pk.grp.kbeg[0] = 0;
@@ -1479,56 +1468,180 @@ int tc_build_dense(fk_table *t, const double *host_fk) {
     pk.ktot = pk.grp.kend[0];
     const int kal = (t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_TF32))) ? 128 : 64;
     pk.ktot_pad = (pk.ktot + kal - 1) / kal * kal;
+    std::vector<int> km(pk.ktot_pad, -1);
+    for (long long k = 0; k < K; ++k) km[k] = km_in.empty() ? (int)k : km_in[k];
+    if (cudaMalloc(&pk.kmeta, km.size() * sizeof(int))) return fail(FK_ENOMEM, "tensor-core gather map");
+    FK_CUDA(cudaMemcpy(pk.kmeta, km.data(), km.size() * sizeof(int), cudaMemcpyHostToDevice));
+    t->bytes += km.size() * sizeof(int);
     const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
     const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
     const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
-    {
-        std::vector<int> km(pk.ktot_pad);
-        for (int k = 0; k < pk.ktot_pad; ++k) km[k] = k < K ? k : -1;
-        if (cudaMalloc(&pk.kmeta, km.size() * sizeof(int))) return fail(FK_ENOMEM, "tensor-core gather map");
-        FK_CUDA(cudaMemcpy(pk.kmeta, km.data(), km.size() * sizeof(int), cudaMemcpyHostToDevice));
-        t->bytes += km.size() * sizeof(int);
-    }
-    const long long rows = (long long)L.ntile_n * L.n_rows;
-    const size_t elems = (size_t)rows * pk.ktot_pad;
+    const size_t elems = (size_t)pk.ntile_n * pk.n_rows * pk.ktot_pad;
     if ((want_hi && cudaMalloc(&pk.hi, elems * 2)) || (want_lo && cudaMalloc(&pk.lo, elems * 2)) ||
         (want_f32 && cudaMalloc(&pk.f32, elems * 4)))
         return fail(FK_ENOMEM, "tensor-core table storage");
     t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+    return FK_OK;
+}
 
-    // FP64 rows on the device for the packing kernels, then freed
+template <int PREC>
+int pack_plain(const TcPack &pk, const double *d_src, int nrows, long long K, cudaStream_t s) {
+    const long long rows = (long long)pk.ntile_n * pk.n_rows;
+    const unsigned blocks = (unsigned)std::min<long long>((rows * pk.ktot_pad + 255) / 256, 148LL * 32);
+    k_pack_dense<PREC><<<blocks, 256, 0, s>>>(d_src, nrows, K, rows, pk.ktot_pad, pk.hi, pk.lo, pk.f32);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+// Copies the host FP64 matrix [nrows][K] to the device, packs it in every
+// tensor-core precision of the table's mask and builds the tensor maps.
+int plain_fill(fk_table *t, TcPack &pk, const double *host, int nrows, long long K) {
+    const bool want_hi = t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3));
+    const bool want_lo = t->mask & FK_PREC_BIT(FK_BF16X3);
+    const bool want_f32 = t->mask & FK_PREC_BIT(FK_TF32);
     double *owned = nullptr;
     cudaStream_t s = nullptr;
     FK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    const size_t src = (size_t)t->ndata * K;
+    const size_t src = (size_t)nrows * K;
     if (cudaMalloc(&owned, src * 8)) {
         cudaStreamDestroy(s);
         return fail(FK_ENOMEM, "tensor-core packing staging");
     }
     int rc = FK_OK;
-    cudaError_t e = cudaMemcpyAsync(owned, host_fk, src * 8, cudaMemcpyHostToDevice, s);
-    if (e) rc = cuda_fail(e, "dense table upload");
-    if (!rc && want_f32) rc = pack_dense<FK_TF32>(t, owned, s);
-    if (!rc && want_lo) rc = pack_dense<FK_BF16X3>(t, owned, s);
-    else if (!rc && want_hi) rc = pack_dense<FK_BF16>(t, owned, s);
+    cudaError_t e = cudaMemcpyAsync(owned, host, src * 8, cudaMemcpyHostToDevice, s);
+    if (e) rc = cuda_fail(e, "table upload for packing");
+    if (!rc && want_f32) rc = pack_plain<FK_TF32>(pk, owned, nrows, K, s);
+    if (!rc && want_lo) rc = pack_plain<FK_BF16X3>(pk, owned, nrows, K, s);
+    else if (!rc && want_hi) rc = pack_plain<FK_BF16>(pk, owned, nrows, K, s);
     if (!rc) {
         e = cudaStreamSynchronize(s);
-        if (e) rc = cuda_fail(e, "dense table packing");
+        if (e) rc = cuda_fail(e, "table packing");
     }
     cudaFree(owned);
     cudaStreamDestroy(s);
     if (rc) return rc;
-    const int h = L.n_rows / 2;  // a multiple of 8 rows
-    if (want_hi && ((rc = make_map(&pk.map_hi, pk.hi, 2, pk.ktot_pad, rows, L.n_rows)) ||
+    const long long rows = (long long)pk.ntile_n * pk.n_rows;
+    const int h = pk.n_rows / 2;  // a multiple of 8 rows
+    if (want_hi && ((rc = make_map(&pk.map_hi, pk.hi, 2, pk.ktot_pad, rows, pk.n_rows)) ||
                     (rc = make_map(&pk.half_hi, pk.hi, 2, pk.ktot_pad, rows, h))))
         return rc;
-    if (want_lo && ((rc = make_map(&pk.map_lo, pk.lo, 2, pk.ktot_pad, rows, L.n_rows)) ||
+    if (want_lo && ((rc = make_map(&pk.map_lo, pk.lo, 2, pk.ktot_pad, rows, pk.n_rows)) ||
                     (rc = make_map(&pk.half_lo, pk.lo, 2, pk.ktot_pad, rows, h))))
         return rc;
-    if (want_f32 && ((rc = make_map(&pk.map_f32, pk.f32, 4, pk.ktot_pad, rows, L.n_rows)) ||
+    if (want_f32 && ((rc = make_map(&pk.map_f32, pk.f32, 4, pk.ktot_pad, rows, pk.n_rows)) ||
                      (rc = make_map(&pk.half_f32, pk.f32, 4, pk.ktot_pad, rows, h))))
         return rc;
     return FK_OK;
+}
+
+}  // namespace
+
+// Dense table (the paper's Table 3 product): the table [ndata][K] is the B
+// operand, the A operand the caller's PDF matrix through the identity map.
+int tc_build_dense(fk_table *t, const double *host_fk) {
+    TcLayout &L = t->tc;
+    L.G = 16;  // not used by the dense epilogue
+    int rc = plain_layout(t, L.fwd, t->ndata, t->E, {});
+    if (rc) return rc;
+    L.n_rows = L.fwd.n_rows;
+    L.ntile_n = L.fwd.ntile_n;
+    return plain_fill(t, L.fwd, host_fk, t->ndata, t->E);
+}
+
+// DIS table: forward packing = the compacted table [ndata][(k, i)] with the A
+// operand gathered from F[r][a_k][xmap[i]]; adjoint packing = its transpose
+// [(k, i)][ndata] with the A operand gO[r][d].
+int tc_build_dis(fk_table *t, const double *host_fk) {
+    TcLayout &L = t->tc;
+    L.G = 16;
+    const int E = (int)t->E;
+    std::vector<int> km(E);
+    for (int e = 0; e < E; ++e) km[e] = t->ca[e / t->nx] * t->nxg + t->xmap[e % t->nx];
+    int rc = plain_layout(t, L.fwd, t->ndata, E, km);
+    if (!rc) rc = plain_fill(t, L.fwd, host_fk, t->ndata, E);
+    if (rc) return rc;
+    std::vector<double> tr((size_t)E * t->ndata);
+    for (int d = 0; d < t->ndata; ++d)
+        for (int e = 0; e < E; ++e) tr[(size_t)e * t->ndata + d] = host_fk[(size_t)d * E + e];
+    rc = plain_layout(t, L.bwd, E, t->ndata, {});
+    if (!rc) rc = plain_fill(t, L.bwd, tr.data(), E, t->ndata);
+    L.n_rows = L.fwd.n_rows;
+    L.ntile_n = L.fwd.ntile_n;
+    return rc;
+}
+
+namespace {
+
+// DIS adjoint scatter: gF[r][a_k][xmap[i]] (+)= P[r][k * nx + i]; the grid
+// points and flavours the table does not use are left alone (zeroed by the
+// caller when overwriting).
+__global__ void k_dis_scatter(const float *__restrict__ P, int R, int E, int nx, int nxg,
+                              const int *__restrict__ ca, const int *__restrict__ xmap, float *__restrict__ gF) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)R * E) return;
+    const int r = (int)(idx / E), e = (int)(idx - (long long)r * E);
+    const int k = e / nx, i = e - k * nx;
+    gF[((size_t)r * NFL + __ldg(ca + k)) * nxg + __ldg(xmap + i)] += P[idx];
+}
+
+template <int PREC>
+int dis_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
+    Scratch scr(s);
+    CUtensorMap mA, mA2;
+    TcParams p;
+    int rc = prepare<PREC>(t, t->tc.fwd, F, R, scr, nullptr, s, mA, mA2, p);
+    if (rc) return rc;
+    // K (active flavours x points, at most 14 x 64) is never split: a
+    // replica's result does not depend on R
+    p.O = O;
+    p.ldo = ldo;
+    return launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.fwd), p, s);
+}
+
+template <int PREC>
+int dis_bwd_tc_t(const fk_table *t, const float *gO, int ldgo, int R, float *gF, int accumulate,
+                 cudaStream_t s) {
+    Scratch scr(s);
+    CUtensorMap mA, mA2;
+    TcParams p;
+    int rc = prepare<PREC>(t, t->tc.bwd, gO, R, scr, nullptr, s, mA, mA2, p, ldgo);
+    if (rc) return rc;
+    const int E = (int)t->E;
+    float *P = nullptr;
+    FK_CUDA(scr.get(&P, (size_t)R * E));
+    p.ndata = E;  // the product's rows are the table's (flavour, x) columns
+    p.O = P;
+    p.ldo = E;
+    rc = launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.bwd), p, s);
+    if (rc) return rc;
+    if (!accumulate) FK_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)R * NFL * t->nxg, s));
+    const long long n = (long long)R * E;
+    k_dis_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, R, E, t->nx, t->nxg, t->d_ca, t->d_xmap, gF);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+}  // namespace
+
+int dis_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s) {
+    switch (prec) {
+        case FK_BF16: return dis_tc_t<FK_BF16>(t, F, R, O, ldo, s);
+        case FK_BF16X3: return dis_tc_t<FK_BF16X3>(t, F, R, O, ldo, s);
+        case FK_TF32: return dis_tc_t<FK_TF32>(t, F, R, O, ldo, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
+}
+
+int dis_bwd_tc(const fk_table *t, const float *gO, int ldgo, int R, float *gF, int accumulate, int prec,
+               cudaStream_t s) {
+    switch (prec) {
+        case FK_BF16: return dis_bwd_tc_t<FK_BF16>(t, gO, ldgo, R, gF, accumulate, s);
+        case FK_BF16X3: return dis_bwd_tc_t<FK_BF16X3>(t, gO, ldgo, R, gF, accumulate, s);
+        case FK_TF32: return dis_bwd_tc_t<FK_TF32>(t, gO, ldgo, R, gF, accumulate, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
 }
 
 int dense_tc(const fk_table *t, const float *Lm, int R, float *O, int ldo, int prec, cudaStream_t s) {

@@ -351,8 +351,6 @@ int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int p
         t = s->tables[table_id];
     }
     if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
-    if (t->kind == FK_KIND_DIS && prec != FK_FP64 && prec != FK_FP32)
-        return fail(FK_EUNSUPPORTED, "DIS tables serve FP64 and FP32 only");
     auto r = std::make_unique<Request>();
     r->table = table_id;
     r->R = R;

@@ -43,14 +43,11 @@ class GlobalFit:
         io = torch.float64 if prec == "fp64" else torch.float32
         if store is None:
             store = ("fp64", "fp32") if prec in ("fp64", "fp32") else (prec,)
-        self.tabs = []
-        for t in tables:
-            st = store if hasattr(t, "ca") else tuple(p for p in store if p in ("fp64", "fp32")) or ("fp32",)
-            self.tabs.append(Table.from_workload(t, st))
+        self.tabs = [Table.from_workload(t, store) for t in tables]
         self.kinds = ["had" if hasattr(t, "ca") else "dis" for t in tables]
-        # DIS tables are small linear contractions: in the reduced modes they
-        # run in FP32 on the CUDA cores (the tensor-core modes are hadronic)
-        self.tprec = [prec if (k == "had" or prec in ("fp64", "fp32")) else "fp32" for k in self.kinds]
+        # every table runs in the step's mode: in the reduced modes the DIS
+        # tables are plain products on the tensor cores, like the hadronic ones
+        self.tprec = [prec for _ in tables]
         nd = [t.ndata for t in tables]
         self.offs = np.concatenate([[0], np.cumsum(nd)]).astype(int)
         self.ntot = int(self.offs[-1])

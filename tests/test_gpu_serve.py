@@ -31,7 +31,7 @@ def setup():
     tabs, kinds = [], []
     for t in g.tables[:10]:
         had = hasattr(t, "ca")
-        precs = ("fp64", "fp32", "bf16", "bf16x3", "tf32") if had else ("fp64", "fp32")
+        precs = ("fp64", "fp32", "bf16", "bf16x3", "tf32")
         tabs.append(fk.Table.from_workload(t, precs=precs))
         kinds.append(had)
     return g, tabs, kinds
@@ -45,7 +45,7 @@ def test_served_results_equal_alone(setup):
     reqs = []
     for n in range(60):
         k = int(rng.integers(len(tabs)))
-        precs = ["fp64", "fp32"] + (["bf16", "bf16x3", "tf32"] if kinds[k] else [])
+        precs = ["fp64", "fp32", "bf16", "bf16x3", "tf32"]
         prec = precs[int(rng.integers(len(precs)))]
         R = int(rng.choice([1, 2, 3, 7, 40, 130]))
         F = W.pdf_replicas(g.x, g.params, R, np.random.default_rng(1000 + n))
@@ -99,13 +99,14 @@ def test_serve_errors(setup):
         srv.submit(7, W.pdf_replicas(g.x, g.params, 1, None), "fp32")
     with pytest.raises(fk.FKError, match="not found"):
         srv.poll(12345)
-    d = [kk for kk, h in enumerate(kinds) if not h]
-    if d:
-        small = fk.Server(budget_bytes=1 << 30, max_inflight=1)
-        tid2 = small.add_table(tabs[d[0]])
-        with pytest.raises(fk.FKError, match="unsupported"):
-            small.submit(tid2, W.pdf_replicas(g.x, g.params, 1, None), "bf16")
-        small.close()
+    # a precision the table does not store
+    d = next(t for t in g.tables if not hasattr(t, "ca"))
+    only64 = fk.Table.from_workload(d, precs=("fp64",))
+    small = fk.Server(budget_bytes=1 << 30, max_inflight=1)
+    tid2 = small.add_table(only64)
+    with pytest.raises(fk.FKError, match="unsupported"):
+        small.submit(tid2, W.pdf_replicas(g.x, g.params, 1, None), "bf16")
+    small.close()
     srv.close()
 
 

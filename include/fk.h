@@ -68,15 +68,28 @@ enum {
  * reduced modes read FP32 F and write FP32 O; the table's stored copy and the
  * packed PDF operand are rounded to the mode's type, products go through the
  * tensor cores and accumulate in FP32.  BF16X3 splits each operand into
- * hi = bf16(v), lo = bf16(v - hi) and sums hi*hi + hi*lo + lo*hi. */
+ * hi = bf16(v), lo = bf16(v - hi) and sums hi*hi + hi*lo + lo*hi.
+ * FP64_TC reads and writes FP64 buffers and gives FP64 results on the tensor
+ * cores: every FP64 operand is split, per row and per K chunk of up to 1024
+ * elements, into 8 exact BF16 digits of 7 bits (each value held to 2^-55 of
+ * the largest of its row in the chunk); the 36 most significant digit
+ * products run as BF16 MMAs whose FP32 sums are exact, and are scaled and
+ * added in FP64 in a fixed order (the slicing of Ozaki et al.).  It is
+ * offered for dense tables (fk_dense_conv), DIS tables (forward and adjoint)
+ * and hadronic tables (forward through the PDF matrix of the paper's Table 3,
+ * adjoint through W = gO FK); the table stores the digit slices (16 bytes
+ * per element, twice for DIS and hadronic tables: one copy per product). */
 enum {
     FK_FP64 = 0,
     FK_FP32 = 1,
     FK_BF16 = 2,
     FK_BF16X3 = 3,
-    FK_TF32 = 4
+    FK_TF32 = 4,
+    FK_FP64_TC = 5
 };
 #define FK_PREC_BIT(p) (1u << (p))
+/* Modes whose buffers are double: FK_FP64 and FK_FP64_TC. */
+#define FK_IO64(p) ((p) == FK_FP64 || (p) == FK_FP64_TC)
 
 /* Table kinds reported by fk_table_info. */
 enum { FK_KIND_DIS = 0, FK_KIND_HAD = 1, FK_KIND_DENSE = 2 };

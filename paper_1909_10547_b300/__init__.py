@@ -52,7 +52,7 @@ def _prec(p):
 
 
 def _io_dtype(prec):
-    return torch.float64 if _prec(prec) == _lib.FK_FP64 else torch.float32
+    return torch.float64 if _prec(prec) in (_lib.FK_FP64, _lib.FK_FP64_TC) else torch.float32
 
 
 def _mask(precs):
@@ -287,7 +287,7 @@ class Server:
 
     def submit(self, table_id: int, F: np.ndarray, prec="fp32") -> int:
         """F: host [R][14][nx_grid] (float64 for fp64, float32 otherwise)."""
-        dt = np.float64 if _prec(prec) == _lib.FK_FP64 else np.float32
+        dt = np.float64 if _prec(prec) in (_lib.FK_FP64, _lib.FK_FP64_TC) else np.float32
         F = np.ascontiguousarray(F, dtype=dt)
         tk = ctypes.c_uint64()
         _lib.call("fk_serve_submit", self._h, int(table_id), _p(F), F.shape[0], _prec(prec),

@@ -106,5 +106,6 @@ def call(name, *args):
 # status codes and precisions (include/fk.h)
 FK_OK, FK_EINVAL, FK_ENOMEM, FK_EBUDGET, FK_EPENDING, FK_ETIMEDOUT, FK_ECUDA, FK_ENOTFOUND, \
     FK_EUNSUPPORTED = range(9)
-FK_FP64, FK_FP32, FK_BF16, FK_BF16X3, FK_TF32 = range(5)
-PRECS = {"fp64": FK_FP64, "fp32": FK_FP32, "bf16": FK_BF16, "bf16x3": FK_BF16X3, "tf32": FK_TF32}
+FK_FP64, FK_FP32, FK_BF16, FK_BF16X3, FK_TF32, FK_FP64_TC = range(6)
+PRECS = {"fp64": FK_FP64, "fp32": FK_FP32, "bf16": FK_BF16, "bf16x3": FK_BF16X3, "tf32": FK_TF32,
+         "fp64tc": FK_FP64_TC}

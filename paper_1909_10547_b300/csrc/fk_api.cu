@@ -27,7 +27,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 namespace {
 
 constexpr unsigned ALL_PRECS = FK_PREC_BIT(FK_FP64) | FK_PREC_BIT(FK_FP32) | FK_PREC_BIT(FK_BF16) |
-                               FK_PREC_BIT(FK_BF16X3) | FK_PREC_BIT(FK_TF32);
+                               FK_PREC_BIT(FK_BF16X3) | FK_PREC_BIT(FK_TF32) | FK_PREC_BIT(FK_FP64_TC);
 constexpr unsigned TC_PRECS = FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_BF16X3) | FK_PREC_BIT(FK_TF32);
 
 void keep_pool() {
@@ -54,6 +54,7 @@ void table_free(fk_table *t) {
     cudaFree(t->fk64);
     cudaFree(t->fk32);
     tc_free(t);
+    oz_free(t);
     delete t;
 }
 
@@ -165,6 +166,13 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
             return rc;
         }
     }
+    if (mask & FK_PREC_BIT(FK_FP64_TC)) {
+        rc = oz_build(t, fk);
+        if (rc) {
+            table_free(t);
+            return rc;
+        }
+    }
     *out = t;
     return FK_OK;
 }
@@ -186,6 +194,7 @@ int dense_create(const double *fk, int ndata, long long K, unsigned mask, fk_tab
     cudaGetDevice(&t->device);
     int rc = upload_rows(t, fk);
     if (!rc && (mask & TC_PRECS)) rc = tc_build_dense(t, fk);
+    if (!rc && (mask & FK_PREC_BIT(FK_FP64_TC))) rc = oz_build(t, fk);
     if (rc) {
         table_free(t);
         return rc;
@@ -200,7 +209,7 @@ int check_conv(const fk_table *t, int kind, const void *F, int R, const void *O,
     if (!F || !O) return fail(FK_EINVAL, "null F or O");
     if (R < 1) return fail(FK_EINVAL, "R < 1");
     if (ldo < 0 || (ldo > 0 && ldo < t->ndata)) return fail(FK_EINVAL, "ldo < ndata");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "unknown precision");
     if (!(t->mask & FK_PREC_BIT(prec)))
         return fail(FK_EUNSUPPORTED, "precision not stored in this table");
     return FK_OK;
@@ -275,6 +284,7 @@ int fk_dis_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
     ldo = ldo ? ldo : t->ndata;
     if (prec == FK_FP64 || prec == FK_FP32)
         return fwd_cc(t, F, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    if (prec == FK_FP64_TC) return oz_dis(t, (const double *)F, R, (double *)O, ldo, (cudaStream_t)stream);
     return dis_tc(t, (const float *)F, R, (float *)O, ldo, prec, (cudaStream_t)stream);
 }
 
@@ -285,6 +295,7 @@ int fk_had_conv(const fk_table *t, const void *F, int R, void *O, int ldo, int p
     ldo = ldo ? ldo : t->ndata;
     if (prec == FK_FP64 || prec == FK_FP32)
         return fwd_cc(t, F, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    if (prec == FK_FP64_TC) return oz_had(t, (const double *)F, R, (double *)O, ldo, (cudaStream_t)stream);
     return fwd_tc(t, (const float *)F, R, (float *)O, ldo, prec, (cudaStream_t)stream);
 }
 
@@ -298,6 +309,7 @@ int fk_dense_conv(const fk_table *t, const void *L, int R, void *O, int ldo, int
     ldo = ldo ? ldo : t->ndata;
     if (prec == FK_FP64 || prec == FK_FP32)
         return dense_cc(t, L, R, O, ldo, prec == FK_FP64, (cudaStream_t)stream);
+    if (prec == FK_FP64_TC) return oz_dense(t, (const double *)L, R, (double *)O, ldo, (cudaStream_t)stream);
     return dense_tc(t, (const float *)L, R, (float *)O, ldo, prec, (cudaStream_t)stream);
 }
 
@@ -306,8 +318,8 @@ int fk_luminosity(const fk_table *t, const void *F, int R, void *L, int prec, fk
     if (t->kind != FK_KIND_HAD) return fail(FK_EINVAL, "the PDF matrix needs a hadronic table");
     if (!F || !L) return fail(FK_EINVAL, "null F or L");
     if (R < 1) return fail(FK_EINVAL, "R < 1");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
-    return luminosity_cc(t, F, R, L, prec == FK_FP64, (cudaStream_t)stream);
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "unknown precision");
+    return luminosity_cc(t, F, R, L, FK_IO64(prec), (cudaStream_t)stream);
 }
 
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
@@ -317,10 +329,13 @@ int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo,
     if (!gO || !gF || (t->kind == FK_KIND_HAD && !F)) return fail(FK_EINVAL, "null F, gO or gF");
     if (R < 1) return fail(FK_EINVAL, "R < 1");
     if (ldgo < 0 || (ldgo > 0 && ldgo < t->ndata)) return fail(FK_EINVAL, "ldgo < ndata");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "unknown precision");
     if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
     const bool f64 = prec == FK_FP64;
     ldgo = ldgo ? ldgo : t->ndata;
+    if (prec == FK_FP64_TC)
+        return oz_bwd(t, (const double *)F, (const double *)gO, ldgo, R, (double *)gF, accumulate ? 1 : 0,
+                      (cudaStream_t)stream);
     if (prec != FK_FP64 && prec != FK_FP32) {  // tensor-core modes
         if (t->kind == FK_KIND_DIS)
             return dis_bwd_tc(t, (const float *)gO, ldgo, R, (float *)gF, accumulate ? 1 : 0, prec,

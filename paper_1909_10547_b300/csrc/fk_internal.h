@@ -97,6 +97,14 @@ struct TcLayout {
     int n_rows = 0;     // MMA N = G * nx rounded up to 16
     TcPack fwd, bwd;
     int8_t *gmap = nullptr;  // device [2][14]: group of flavour a in fwd / bwd packing, or -1
+    // FP64 on the tensor cores (k_oz.cu): the table as exact BF16 digit
+    // slices, rows [ndata] over K (oz) and, for the adjoints, rows over K
+    // = ndata (ozT: DIS [(k, i)][d], hadronic [(c, i, j)][d]); hi holds the
+    // S slices stacked [S][ntile_n * n_rows][ktot_pad], oz_e the exponent
+    // of each (row, K chunk)
+    TcPack oz, ozT;
+    int *oz_e = nullptr, *ozT_e = nullptr;
+    int oz_kchunk = 0, ozT_kchunk = 0;
 };
 
 }  // namespace fk
@@ -156,6 +164,17 @@ int dis_bwd_tc(const fk_table *t, const float *gO, int ldgo, int R, float *gF, i
 int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
            int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);
+// operand-slice products (k_tc.cu) and FP64 on the tensor cores (k_oz.cu)
+int tc_map_bf16(CUtensorMap *m, const void *ptr, long long cols, long long rows, int box_rows);
+int tc_slice_pairs(const fk_table *t, const TcPack &pk, const CUtensorMap &mA, int R, int nd_out, int kchunk,
+                   int c0, int nsplit, int npair, const uint8_t *pa, const uint8_t *pb, float *P, cudaStream_t s);
+int oz_build(fk_table *t, const double *host_fk);
+void oz_free(fk_table *t);
+int oz_dense(const fk_table *t, const double *L, int R, double *O, int ldo, cudaStream_t s);
+int oz_dis(const fk_table *t, const double *F, int R, double *O, int ldo, cudaStream_t s);
+int oz_had(const fk_table *t, const double *F, int R, double *O, int ldo, cudaStream_t s);
+int oz_bwd(const fk_table *t, const double *F, const double *gO, int ldgo, int R, double *gF, int accumulate,
+           cudaStream_t s);
 // FK_ETIMEDOUT if a kernel's bounded wait ran out since the last reset
 // (device_status: tensor-core kernels; cc_device_status: CUDA-core kernels)
 int device_status(int reset);

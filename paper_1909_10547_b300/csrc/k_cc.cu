@@ -1102,9 +1102,9 @@ extern "C" int fk_grad_sum(const void *const *parts, int nparts, long long n, vo
         return fail(FK_EINVAL, "fk_grad_sum: bad arguments (1 <= nparts <= 64)");
     for (int k = 0; k < nparts; ++k)
         if (!parts[k]) return fail(FK_EINVAL, "fk_grad_sum: null part");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_grad_sum: unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "fk_grad_sum: unknown precision");
     if (n == 0) return FK_OK;
-    return prec == FK_FP64 ? grad_sum_t<double>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream)
+    return FK_IO64(prec) ? grad_sum_t<double>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream)
                            : grad_sum_t<float>(parts, nparts, n, out, accumulate ? 1 : 0, (cudaStream_t)stream);
 }
 

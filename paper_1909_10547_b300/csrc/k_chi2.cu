@@ -434,8 +434,8 @@ int fk_cov_size(const fk_cov *cov) { return cov ? cov->n : 0; }
 int fk_chi2(const fk_cov *cov, const void *O, const double *D, int R, double *chi2, void *gO,
             int io_prec, fk_stream stream) {
     if (!cov || !O || !D || !chi2 || R < 1) return fk::fail(FK_EINVAL, "fk_chi2: null pointer or R < 1");
-    if (io_prec < FK_FP64 || io_prec > FK_TF32) return fk::fail(FK_EINVAL, "fk_chi2: unknown precision");
-    if (io_prec == FK_FP64)
+    if (io_prec < FK_FP64 || io_prec > FK_FP64_TC) return fk::fail(FK_EINVAL, "fk_chi2: unknown precision");
+    if (FK_IO64(io_prec))
         return fk::chi2_t<double>(cov, (const double *)O, D, R, chi2, (double *)gO, (cudaStream_t)stream);
     return fk::chi2_t<float>(cov, (const float *)O, D, R, chi2, (float *)gO, (cudaStream_t)stream);
 }

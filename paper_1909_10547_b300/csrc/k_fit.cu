@@ -81,10 +81,10 @@ int fk_pdf_eval(const void *theta, int R, const double *x_grid, int nx_grid, voi
                 fk_stream stream) {
     if (!theta || !x_grid || !F || R < 1 || nx_grid < 1 || nx_grid > MAX_NXG)
         return fail(FK_EINVAL, "fk_pdf_eval: bad arguments");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_pdf_eval: unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "fk_pdf_eval: unknown precision");
     const long long n = (long long)R * NFL * nx_grid;
     const cudaStream_t s = (cudaStream_t)stream;
-    if (prec == FK_FP64)
+    if (FK_IO64(prec))
         k_pdf_eval<double><<<blocks_for(n), 256, 0, s>>>((const double *)theta, R, x_grid, nx_grid, (double *)F);
     else
         k_pdf_eval<float><<<blocks_for(n), 256, 0, s>>>((const float *)theta, R, x_grid, nx_grid, (float *)F);
@@ -97,11 +97,11 @@ int fk_pdf_grad(const void *F, const void *gF, int R, const double *x_grid, int 
                 int prec, fk_stream stream) {
     if (!F || !gF || !x_grid || !gtheta || R < 1 || nx_grid < 1 || nx_grid > MAX_NXG)
         return fail(FK_EINVAL, "fk_pdf_grad: bad arguments");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_pdf_grad: unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "fk_pdf_grad: unknown precision");
     const long long warps = (long long)R * NFL;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
     const cudaStream_t s = (cudaStream_t)stream;
-    if (prec == FK_FP64)
+    if (FK_IO64(prec))
         k_pdf_grad<double><<<blocks, 256, 0, s>>>((const double *)F, (const double *)gF, R, x_grid, nx_grid,
                                                   (double *)gtheta);
     else
@@ -117,11 +117,11 @@ int fk_adam_step(void *p, const void *g, void *m, void *v, long long n, int t, d
     if (!p || !g || !m || !v || n < 0 || t < 1 || !(lr > 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) ||
         !(eps > 0))
         return fail(FK_EINVAL, "fk_adam_step: bad arguments");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_adam_step: unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "fk_adam_step: unknown precision");
     if (n == 0) return FK_OK;
     const double c1 = 1.0 - std::pow(b1, t), c2 = 1.0 - std::pow(b2, t);
     const cudaStream_t s = (cudaStream_t)stream;
-    if (prec == FK_FP64)
+    if (FK_IO64(prec))
         k_adam<double><<<blocks_for(n), 256, 0, s>>>((double *)p, (const double *)g, (double *)m, (double *)v, n, lr,
                                                      b1, b2, eps, c1, c2);
     else

@@ -311,6 +311,14 @@ struct TcParams {
     // element sp * kspl and writes its partial tile at O + sp * ostride
     int ntile_n, nsplit, kspl;
     long long ostride;
+    // operand slices (FP64 on the tensor cores): work items also run over
+    // npair (A slice, B slice) pairs; pair u reads A rows from
+    // pa[u] * a_rows and B rows from pb[u] * b_rows and writes its partial
+    // tiles at O + (u * nsplit + sp) * ostride.  npair = 1, pa = pb = 0 for
+    // every other product.
+    int npair, a_rows, b_rows;
+    uint8_t pa[64], pb[64];
+    int kbase;  // K element where split 0 starts
 };
 
 // Epilogue modes of the tensor-core kernel.
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int w_first = CL == 2 ? (int)cluster_id() : (int)blockIdx.x;
     const int w_step = CL == 2 ? (int)cluster_count() : (int)gridDim.x;
     const int w_count = p.ntiles / CL;
-    auto tile_of = [&](int w, int &rt, int &nt, int &sp) {
+    auto tile_of = [&](int w, int &rt, int &nt, int &sp, int &pr) {
         if (CL == 2) {
             const int half = p.nrt / 2;
             nt = w / half;
@@ -360,6 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         sp = nt / p.ntile_n;
         nt -= sp * p.ntile_n;
+        pr = sp / p.nsplit;
+        sp -= pr * p.nsplit;
     };
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -435,11 +445,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int it = 0, pgc = 0;  // pgc: accumulator uses (groups) reached so far
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
-            int rt, nt;
-            int sp;
-            tile_of(w, rt, nt, sp);
-            const int brow = nt * p.n_rows + (int)rank * b_rows;
-            const int koff = sp * p.kspl;  // the split's first K element
+            int rt, nt, sp, pr;
+            tile_of(w, rt, nt, sp, pr);
+            const int brow = p.pb[pr] * p.b_rows + nt * p.n_rows + (int)rank * b_rows;
+            const int arow = p.pa[pr] * p.a_rows + rt * TC_M;
+            const int koff = p.kbase + sp * p.kspl;  // the split's first K element
             int pg = 0;  // next group whose first stage is still to be loaded
             for (int q = 0; q < p.nchunks; ++q, ++it) {
                 const int s = it % S;
@@ -467,10 +477,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
                         const int x = koff + q * T::KCS + a * T::KC;
-                        tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, rt * TC_M);
+                        tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, arow);
                         tma_load_2d_pair(st + offB + a * b_bytes, &mapB, fb, x, brow);
                         if (T::X3) {
-                            tma_load_2d_pair(st + offA2 + a * a_bytes, &mapA2, fb, x, rt * TC_M);
+                            tma_load_2d_pair(st + offA2 + a * a_bytes, &mapA2, fb, x, arow);
                             tma_load_2d_pair(st + offB2 + a * b_bytes, &mapB2, fb, x, brow);
                         }
                     }
@@ -479,10 +489,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
                         const int x = koff + q * T::KCS + a * T::KC;
-                        tma_load_2d(st + a * a_bytes, &mapA, full(s), x, rt * TC_M);
+                        tma_load_2d(st + a * a_bytes, &mapA, full(s), x, arow);
                         tma_load_2d(st + offB + a * b_bytes, &mapB, full(s), x, brow);
                         if (T::X3) {
-                            tma_load_2d(st + offA2 + a * a_bytes, &mapA2, full(s), x, rt * TC_M);
+                            tma_load_2d(st + offA2 + a * a_bytes, &mapA2, full(s), x, arow);
                             tma_load_2d(st + offB2 + a * b_bytes, &mapB2, full(s), x, brow);
                         }
                     }
@@ -645,9 +655,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int gc = 0;
         bool ok = true;
         for (int w = w_first; w < w_count && ok; w += w_step) {
-            int rt, nt;
-            int sp;
-            tile_of(w, rt, nt, sp);
+            int rt, nt, sp, pr;
+            tile_of(w, rt, nt, sp, pr);
             const int r = rt * TC_M + rl;
             float acc[G];
 #pragma unroll
@@ -697,7 +706,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             uint32_t v[64];
                             tmem_ld64(taddr + (uint32_t)(c * 64), v);
                             if (r < p.R) {
-                                float *orow = p.O + sp * p.ostride + (size_t)r * p.ldo + dbase + c * 64;
+                                float *orow = p.O + ((long long)pr * p.nsplit + sp) * p.ostride + (size_t)r * p.ldo +
+                                              dbase + c * 64;
 #pragma unroll
                                 for (int k = 0; k < 64; ++k)
                                     if (dbase + c * 64 + k < p.ndata) orow[k] = __uint_as_float(v[k]);
@@ -1169,6 +1179,7 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     if (rc) return rc;
     if (PREC != FK_BF16X3) mA2 = mA;
     p = TcParams{};
+    p.npair = 1;  // pa = pb = 0: one operand pair
     p.nrt = R_pad / TC_M;
     p.ntiles = pk.ntile_n * p.nrt;
     p.ntile_n = pk.ntile_n;
@@ -1744,3 +1755,52 @@ int fk_wait_selftest(int limit_us) {
     if (rc != FK_OK) return rc;
     return fail(FK_ECUDA, "fk_wait_selftest: the bounded wait did not report");
 }
+
+// ---------------------------------------------- operand slices (k_oz.cu) ----
+namespace fk {
+
+int tc_map_bf16(CUtensorMap *m, const void *ptr, long long cols, long long rows, int box_rows) {
+    return make_map(m, ptr, 2, cols, rows, box_rows);
+}
+
+// The BF16 products of npair (A slice, B slice) pairs over K chunks c0 ..
+// c0 + nsplit - 1 of kchunk elements (a multiple of 128): A map over [S * R_pad][ktot_pad]
+// (slice u's rows start at pa[u] * R_pad), B the pack's stacked slices
+// (pb[u] * ntile_n * n_rows); partial tile (u, sp) lands at
+// P + (u * nsplit + sp) * R * nd_out, [R][nd_out].  The last chunk may run
+// past the operands' K, which the tensor maps read as zeros.
+int tc_slice_pairs(const fk_table *t, const TcPack &pk, const CUtensorMap &mA, int R, int nd_out, int kchunk,
+                   int c0, int nsplit, int npair, const uint8_t *pa, const uint8_t *pb, float *P, cudaStream_t s) {
+    if (npair < 1 || npair > 64 || kchunk % Tr<FK_BF16>::KCS)
+        return fail(FK_EINVAL, "tc_slice_pairs: bad pair count or chunk");
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    TcParams p{};
+    p.nrt = R_pad / TC_M;
+    p.ntile_n = pk.ntile_n;
+    p.n_rows = pk.n_rows;
+    p.nbl = pk.n_rows <= 128 ? 2 : 1;
+    p.ngroups = 1;
+    p.kbeg[0] = 0;
+    p.kend[0] = kchunk;
+    p.kspl = kchunk;
+    p.kbase = c0 * kchunk;
+    p.nchunks = kchunk / Tr<FK_BF16>::KCS;
+    p.nsplit = nsplit;
+    p.npair = npair;
+    for (int u = 0; u < npair; ++u) {
+        p.pa[u] = pa[u];
+        p.pb[u] = pb[u];
+    }
+    p.a_rows = R_pad;
+    p.b_rows = pk.ntile_n * pk.n_rows;
+    p.ndata = nd_out;
+    p.R = R;
+    p.R_pad = R_pad;
+    p.O = P;
+    p.ldo = nd_out;
+    p.ostride = (long long)R * nd_out;
+    p.ntiles = p.nrt * p.ntile_n * nsplit * npair;
+    return launch_tc<FK_BF16, 16, MODE_DENSE>(t, mA, mA, b_maps<FK_BF16>(pk), p, s);
+}
+
+}  // namespace fk

@@ -107,10 +107,15 @@ size_t pow2_class(size_t n) {
 
 // Device bytes a launch of R replicas on table t needs besides the table.
 size_t request_device_bytes(const fk_table *t, int R, int prec) {
-    const size_t esz = prec == FK_FP64 ? 8 : 4;
+    const size_t esz = FK_IO64(prec) ? 8 : 4;
     size_t b = esz * (size_t)R * NFL * t->nxg + esz * (size_t)R * t->ndata;
     if (prec == FK_FP64 || prec == FK_FP32) {
         b += esz * (size_t)R * t->ndata * 256;  // partial sums (the split is at most 196)
+    } else if (prec == FK_FP64_TC) {
+        // digit slices of the replicas' operand (8 x 2 bytes per element), the
+        // PDF matrix (hadronic) and up to 1 GiB of exact partial tiles
+        const size_t rpad = (size_t)(R + 127) / 128 * 128;
+        b += rpad * t->tc.oz.ktot_pad * 16 + (t->kind == FK_KIND_HAD ? 8 * (size_t)R * t->E : 0) + (1ull << 30);
     } else {
         const size_t rpad = (size_t)(R + 127) / 128 * 128;
         b += rpad * t->tc.fwd.ktot_pad * (prec == FK_TF32 ? 4 : (prec == FK_BF16X3 ? 4 : 2)) +
@@ -174,7 +179,7 @@ void CUDART_CB batch_done(void *arg) {
 void launch_batch(fk_server *s, Batch *b) {
     const fk_table *t = s->tables[b->reqs[0]->table];
     const int prec = b->reqs[0]->prec;
-    const size_t esz = prec == FK_FP64 ? 8 : 4;
+    const size_t esz = FK_IO64(prec) ? 8 : 4;
     int R = 0;
     for (Request *r : b->reqs) R += r->R;
     cudaStream_t st = s->streams[b->stream];
@@ -232,6 +237,7 @@ void launch_batch(fk_server *s, Batch *b) {
 // streams R = 1 and uses the factorised kernel for R >= 2 (DIS: R <= 4 and
 // R > 4); each tensor-core precision is a single class.
 int kernel_class(const fk_table *t, int prec, int R) {
+    if (prec == FK_FP64_TC) return 3;
     if (prec != FK_FP64 && prec != FK_FP32) return 2;
     if (t->kind == FK_KIND_HAD) return R == 1 ? 0 : 1;
     return R <= 4 ? 0 : 1;
@@ -355,7 +361,7 @@ int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int p
     r->table = table_id;
     r->R = R;
     r->prec = prec;
-    const size_t esz = prec == FK_FP64 ? 8 : 4;
+    const size_t esz = FK_IO64(prec) ? 8 : 4;
     r->f_bytes = esz * (size_t)R * NFL * t->nxg;
     r->o_bytes = esz * (size_t)R * t->ndata;
     r->dev_bytes = request_device_bytes(t, R, prec);

@@ -40,7 +40,7 @@ class GlobalFit:
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
         self.prec = prec
-        io = torch.float64 if prec == "fp64" else torch.float32
+        io = torch.float64 if prec in ("fp64", "fp64tc") else torch.float32
         if store is None:
             store = ("fp64", "fp32") if prec in ("fp64", "fp32") else (prec,)
         self.tabs = [Table.from_workload(t, store) for t in tables]

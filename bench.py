@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32", "fp64tc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner", type=int, default=10,
@@ -104,7 +104,7 @@ def peak_of(prec, pk, sustained=False):
     """(TFLOP/s, source) of the arithmetic a mode runs on: the tensor pipe for
     BF16 / BF16 hi+lo (BF16 peak) and TF32, the CUDA cores for FP32 and FP64."""
     mhz = pk.get("sm_max_mhz", 2032.0)
-    if prec in ("bf16", "bf16x3"):
+    if prec in ("bf16", "bf16x3", "fp64tc"):
         return (pk["bf16_tflops_sustained"] if sustained else pk["bf16_tflops"]), "measured (cuBLAS BF16)"
     if prec == "tf32":
         if "tf32_tflops" in pk:
@@ -376,7 +376,17 @@ def roof_entry(prec, byts, flops, ms, kernel, traffic=None):
     pk, src = peaks()
     tpeak, psrc = peak_of(prec, pk)
     ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
-    tc = prec in ("bf16", "bf16x3", "tf32")
+    tc = prec in ("bf16", "bf16x3", "tf32", "fp64tc")
+    if prec == "fp64tc":
+        # FP64 results from 36 BF16 digit products per multiply-add: the
+        # tensor pipe's issued rate against the BF16 peak, and the useful FP64
+        # rate against the FP64 pipe's
+        iss = ISSUED[prec] * flops / (ms * 1e-3) / 1e12
+        f64pk, f64src = peak_of("fp64", pk)
+        return {"bound": "tensor", "achieved": iss, "peak": tpeak, "unit": "TFLOP/s", "frac": iss / tpeak,
+                "issued": True, "useful_tflops": flops / (ms * 1e-3) / 1e12,
+                "useful_vs_fp64_peak": flops / (ms * 1e-3) / 1e12 / f64pk, "fp64_peak_source": f64src,
+                "algorithmic_flops": flops, "peak_source": psrc, "traffic": traffic, "kernel": kernel}
     if flops / byts < ridge:
         ach = byts / (ms * 1e-3) / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
@@ -518,7 +528,7 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0):
         if key not in pool:
             x = g.x if key[0] == 50 else W.xgrid(key[0], 1e-7)
             F = W.pdf_replicas(x, g.params, key[1], np.random.default_rng(key[1]))
-            pool[key] = F.astype(np.float64 if key[2] == "fp64" else np.float32)
+            pool[key] = F.astype(np.float64 if key[2] in ("fp64", "fp64tc") else np.float32)
     work = [(int(which[k]), pool[(nxg[which[k]], int(Rs[k]), allprec[which[k]])], allprec[which[k]])
             for k in range(n)]
     units = sum(alltabs[w].ndata * F.shape[0] for w, F, _ in work)
@@ -689,7 +699,10 @@ def run_reference(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
-ESZ = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4, "tf32": 4}  # table bytes per element
+# table bytes per element of the definition in each mode (FP64_TC: the FP64 values it reproduces)
+ESZ = {"fp64": 8, "fp32": 4, "bf16": 2, "bf16x3": 4, "tf32": 4, "fp64tc": 8}
+# MMAs issued per multiply-add of the definition
+ISSUED = {"bf16x3": 3, "fp64tc": 36}
 
 
 def roofline(fit, seg, prec):
@@ -796,12 +809,13 @@ def run_dense(args):
     t, F = W.table3(nd, R)
     K = t.fk[0].size
     prec = args.prec
-    io = torch.float64 if prec == "fp64" else torch.float32
-    ht = fk.Table.from_workload(t, precs=("fp64" if prec == "fp64" else "fp32",))
+    f64 = prec in ("fp64", "fp64tc")
+    io = torch.float64 if f64 else torch.float32
+    ht = fk.Table.from_workload(t, precs=("fp64" if f64 else "fp32",))
     tab = fk.Table.dense(t.fk.reshape(nd, K), precs=(prec,))
     del t
     Fd = torch.tensor(F, dtype=io, device="cuda")
-    L = fk.luminosity(ht, Fd, "fp64" if prec == "fp64" else "fp32")
+    L = fk.luminosity(ht, Fd, "fp64" if f64 else "fp32")
     O = fk.dense_conv(tab, L, prec)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -892,7 +906,7 @@ def run_stress(args):
         F = W.pdf_replicas(x, W.pdf_params(np.random.default_rng(1)), R, np.random.default_rng(2) if R > 1 else None)
         name = f"hadronic stress table {args.ndata} x 196 channels x 50 x 50, one convolution, R={R}"
     tab = fk.Table.from_workload(t, precs=(args.prec,))
-    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    dt = torch.float64 if args.prec in ("fp64", "fp64tc") else torch.float32
     Fd = torch.tensor(F, dtype=dt, device="cuda")
     O = fk.conv(tab, Fd, args.prec)
     torch.cuda.synchronize()
@@ -915,23 +929,12 @@ def run_stress(args):
     elems = t.fk.size
     byts = elems * ESZ[args.prec]
     flops = 2.0 * elems * R
-    pk, src = peaks()
-    tc = args.prec in ("bf16", "bf16x3", "tf32")
-    tpeak, _ = peak_of(args.prec, pk)
-    ridge = tpeak * 1e12 / (pk["hbm_gbs"] * 1e9)
-    if flops / byts < ridge:
-        ach = byts / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "algorithmic_bytes": byts}
-    else:
-        ach = flops / (ms * 1e-3) / 1e12
-        roof = {"bound": "tensor" if tc else "alu", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s",
-                "frac": ach / tpeak, "traffic": None}
-    roof["peak_source"] = src
-    kern = "k_tc" if tc else ("k_stream" if R == 1 else "k_fac")
-    if kern:
-        roof["kernel"] = f"{kern} (timed as the whole convolution call, operand packing included)"
-        roof["traffic"] = traffic_of(kern, args.prec, args.ndata, R) if args.table == "stress" else None
+    tc = args.prec in ("bf16", "bf16x3", "tf32", "fp64tc")
+    kern = ("k_oz_slice + k_tc digit pairs + k_oz_combine" if args.prec == "fp64tc" else
+            "k_tc" if tc else ("k_stream" if R == 1 else "k_fac"))
+    roof = roof_entry(args.prec, byts, flops, ms, f"{kern} (timed as the whole convolution call)",
+                      traffic_of(kern, args.prec, args.ndata, R) if args.table == "stress" and args.prec != "fp64tc"
+                      else None)
     line = {"metric": METRIC, "value": args.ndata * R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
@@ -974,7 +977,7 @@ def run_serve(args):
         if key not in pool:
             x = g.x if key[0] == 50 else W.xgrid(key[0], 1e-7)
             F = W.pdf_replicas(x, g.params, key[1], np.random.default_rng(key[1]))
-            pool[key] = F.astype(np.float64 if key[2] == "fp64" else np.float32)
+            pool[key] = F.astype(np.float64 if key[2] in ("fp64", "fp64tc") else np.float32)
     work = [(int(which[k]), pool[(nxg[which[k]], int(Rs[k]), tprec[which[k]])], tprec[which[k]]) for k in range(n)]
     units = sum(tabs[w].ndata * F.shape[0] for w, F, _ in work)
 
@@ -1036,7 +1039,7 @@ def run_serve(args):
     plain_lat = []
     for w, F, p in work:
         s0 = time.perf_counter()
-        dt = torch.float64 if p == "fp64" else torch.float32
+        dt = torch.float64 if p in ("fp64", "fp64tc") else torch.float32
         Fd = torch.from_numpy(F).to("cuda", non_blocking=False)
         O = fk.conv(tabs[w], Fd, p)
         O.cpu()
@@ -1225,7 +1228,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16",
-                                           "bf16x3": "bf16x3", "tf32": "tf32"}[args.prec],
+                                           "bf16x3": "bf16x3", "tf32": "tf32", "fp64tc": "f64 (bf16 digit slices)"}[args.prec],
             "data": "synthetic",
             "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
                            schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves",

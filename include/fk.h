@@ -70,7 +70,7 @@ enum {
  * tensor cores and accumulate in FP32.  BF16X3 splits each operand into
  * hi = bf16(v), lo = bf16(v - hi) and sums hi*hi + hi*lo + lo*hi.
  * FP64_TC reads and writes FP64 buffers and gives FP64 results on the tensor
- * cores: every FP64 operand is split, per row and per K chunk of up to 1024
+ * cores: every FP64 operand is split, per row and per K chunk of up to 512
  * elements, into 8 exact BF16 digits of 7 bits (each value held to 2^-55 of
  * the largest of its row in the chunk); the 36 most significant digit
  * products run as BF16 MMAs whose FP32 sums are exact, and are scaled and

@@ -167,7 +167,8 @@ void tc_free(fk_table *t);
 // operand-slice products (k_tc.cu) and FP64 on the tensor cores (k_oz.cu)
 int tc_map_bf16(CUtensorMap *m, const void *ptr, long long cols, long long rows, int box_rows);
 int tc_slice_pairs(const fk_table *t, const TcPack &pk, const CUtensorMap &mA, int R, int nd_out, int kchunk,
-                   int c0, int nsplit, int npair, const uint8_t *pa, const uint8_t *pb, float *P, cudaStream_t s);
+                   int c0, int nsplit, int npair, int npc, const uint8_t *pa, const uint8_t *pb, float *P,
+                   cudaStream_t s);
 int oz_build(fk_table *t, const double *host_fk);
 void oz_free(fk_table *t);
 int oz_dense(const fk_table *t, const double *L, int R, double *O, int ldo, cudaStream_t s);

@@ -1,22 +1,21 @@
 // FP64 results on the tensor cores by exact operand slices (the splitting of
 // Ozaki et al.): the FK_FP64_TC mode.
 //
-// Every FP64 operand row is cut along K into chunks of up to 1024 elements;
+// Every FP64 operand row is cut along K into chunks of up to 512 elements;
 // within a chunk each value v is written as
 //   v = 2^(e - S*B) * sum_{p=0}^{S-1} t_p 2^(B (S-1-p)),   |t_p| <= 64,
 // with e the exponent of the chunk's largest |v| plus one (so the scaled value
 // is below 2^(S*B - 1)), B = 7 bits per digit and S = 8 digits: every value
 // to within 2^-55 of the largest one of its row in the chunk, and every value
-// of at least 1/8 of that largest one exactly.  A digit is a small
-// integer, exact in BF16.  The product of digit slices p (A side) and q (B
-// side) over one chunk is a sum of at most 1024 products of integers below
-// 2^6 in magnitude, so the tensor cores' FP32 accumulation of it is exact.
-// The kernel runs the 36 most significant pairs (p + q <= S - 1) of every
-// chunk as plain BF16 MMAs (k_tc, dense mode, one pass over all pairs and
-// chunks); k_oz_combine scales each exact partial by its power of two and adds
-// them in FP64, chunks in order and pairs in a fixed order within a chunk.
-// Each of the 28 dropped pairs (p + q >= S) is below 2^-56 of the chunk's
-// largest digit product.
+// of at least 1/8 of that largest one exactly.  A digit is a small integer,
+// exact in BF16.  The 36 most significant digit products (p + q = w <= S - 1)
+// run as BF16 MMAs over the chunk; the w + 1 products of one weight w
+// accumulate in one accumulator: at most 8 x 512 products of integers of at
+// most 2^6 in magnitude, a sum of at most 2^24 in magnitude, so the tensor
+// cores' FP32 accumulation of it is exact.  k_oz_combine scales each of the 8
+// exact partials of a chunk by its power of two and adds them in FP64, chunks
+// in order and weights in order.  Each of the 28 dropped digit products
+// (w >= S) is below 2^-56 of the chunk's largest one.
 //
 // Served products: the dense tables of the paper's Table 3 (O = FK L), DIS
 // tables (forward: FK times the gathered PDF; adjoint: gO times the
@@ -35,24 +34,16 @@ namespace {
 
 constexpr int OZ_S = 8;         // digits per value
 constexpr int OZ_B = 7;         // bits per digit
-constexpr int OZ_CHUNK = 1024;  // K per exact FP32 accumulation
+constexpr int OZ_CHUNK = 512;   // K per exact FP32 accumulation of one weight
 constexpr size_t OZ_PART_BYTES = 1ull << 30;  // partial tiles per launch
 
-struct Pairs {
-    int n = 0;
-    uint8_t a[64], b[64];
-};
-
-// (p, q) with p + q <= S - 1, most significant first
-Pairs oz_pairs() {
-    Pairs P;
-    for (int w = 0; w < OZ_S; ++w)
-        for (int p = 0; p <= w; ++p) {
-            P.a[P.n] = (uint8_t)p;
-            P.b[P.n] = (uint8_t)(w - p);
-            ++P.n;
-        }
-    return P;
+// the pairs (p, q) of weight w = p + q, p ascending
+int weight_pairs(int w, uint8_t *pa, uint8_t *pb) {
+    for (int p = 0; p <= w; ++p) {
+        pa[p] = (uint8_t)p;
+        pb[p] = (uint8_t)(w - p);
+    }
+    return w + 1;
 }
 
 // grid rows_pad * nchunk (block b: row b / nchunk, chunk b % nchunk), 256
@@ -61,6 +52,31 @@ Pairs oz_pairs() {
 // src[row * ld + kmeta[k]] (kmeta[k] < 0: zero).  Rows >= nrows and columns
 // >= K (without kmeta) are zero.  out: [S][rows_pad][ktot_pad] digits,
 // ex: [rows_pad][nchunk] chunk exponents.
+__device__ __forceinline__ long long abs_bits(double v) {
+    return __double_as_longlong(v) & 0x7fffffffffffffffLL;  // ordered like |v| for every double
+}
+
+// N = round(v 2^(S*B - e)) (ties away from zero), computed on the integer
+// pipe from v's bits: v = m 2^(ev - 1075) with the 53-bit significand m.
+__device__ __forceinline__ long long scaled_int(double v, int e) {
+    const long long bits = __double_as_longlong(v);
+    int ev = (int)((bits >> 52) & 0x7ff);
+    long long m = bits & ((1LL << 52) - 1);
+    if (ev == 0)
+        ev = 1;  // subnormal: no implicit bit
+    else
+        m |= 1LL << 52;
+    const int sh = ev - 1075 + OZ_S * OZ_B - e;  // N = m 2^sh, |N| <= 2^(S*B - 1)
+    long long N;
+    if (sh >= 0)
+        N = m << sh;
+    else if (sh > -60)
+        N = (m + (1LL << (-sh - 1))) >> (-sh);
+    else
+        N = 0;
+    return bits < 0 ? -N : N;
+}
+
 __global__ void __launch_bounds__(256) k_oz_slice(const double *__restrict__ src, long long ld, int nrows, long long K,
                                                   const int *__restrict__ kmeta, int trans, int rows_pad,
                                                   int ktot_pad, int kchunk, int nchunk,
@@ -69,7 +85,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *__restrict__ src
     const int k0 = c * kchunk, kn = min(kchunk, ktot_pad - k0);
     constexpr int PER = OZ_CHUNK / 256;
     double v[PER];
-    double mx = 0.0;
+    long long mx = 0;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int kk = threadIdx.x + 256 * j;
@@ -79,44 +95,52 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *__restrict__ src
             long long col = kmeta ? (long long)__ldg(kmeta + k) : (k < K ? k : -1);
             if (col >= 0) v[j] = trans ? src[col * ld + row] : src[(long long)row * ld + col];
         }
-        mx = fmax(mx, fabs(v[j]));
+        mx = max(mx, abs_bits(v[j]));
     }
-    __shared__ double red[8];
+    __shared__ long long red[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (long long)__shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
     mx = red[0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
-    // mx < 2^(ilogb(mx) + 1): with e = ilogb(mx) + 2 the scaled values stay
-    // below 2^(S*B - 1), so the leading digit is at most 2^(B-1) = 64
-    const int e = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    for (int w = 1; w < 8; ++w) mx = max(mx, red[w]);
+    // largest |v| below 2^(ilogb + 1): with e = ilogb + 2 the scaled values
+    // stay at or below 2^(S*B - 1), so every digit is at most 2^(B-1) = 64
+    const int e = mx > 0 ? ilogb(__longlong_as_double(mx)) + 2 : 0;
     if (threadIdx.x == 0) ex[(size_t)row * nchunk + c] = e;
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int kk = threadIdx.x + 256 * j;
         if (kk >= kn) continue;
-        double x = ldexp(v[j], OZ_S * OZ_B - e);
+        long long N = scaled_int(v[j], e);
+        // balanced base-2^B digits from the top: each digit rounds the
+        // remainder (ties up), which then lies in [-2^(sh-1), 2^(sh-1))
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p) {
             const int sh = OZ_B * (OZ_S - 1 - p);
-            const double t = rint(ldexp(x, -sh));
-            x -= ldexp(t, sh);  // exact: the remainder is below 2^(sh - 1)
+            const long long t = sh ? (N + (1LL << (sh - 1))) >> sh : N;
+            N -= t * (1LL << sh);
             out[((size_t)p * rows_pad + row) * ktot_pad + k0 + kk] = __float2bfloat16_rn((float)t);
         }
     }
 }
 
-struct PairArg {
-    uint8_t a[64], b[64];
-};
+// 2^k as a double (k within the normal range; ldexp outside it)
+__device__ __forceinline__ double pow2(int k) {
+    return (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(k + 1023) << 52) : ldexp(1.0, k);
+}
 
-// O[r][d] (+)= sum_{c in [c0, c0 + nc)} sum_u 2^(ea[r][c] + eb[d][c] - 2 S B + B (2S - 2 - a_u - b_u)) P[u][c - c0][r][d],
-// chunks in order, pairs in order (accumulate: starting from O).
-__global__ void k_oz_combine(const float *__restrict__ P, int npair, PairArg pr, int c0, int nc, int nchunk,
-                             int R, int nd, const int *__restrict__ ea, const int *__restrict__ eb,
-                             double *__restrict__ O, int ldo, int accumulate) {
+// O[r][d] (+)= sum_{c in [c0, c0 + nc)} 2^(ea[r][c] + eb[d][c] - 2 S B + B (2S - 2))
+//                 * sum_{w < S} 2^(-B w) P[w][c - c0][r][d],
+// chunks in order (accumulate: starting from O).  The partials are exact
+// integers (at most 2^24): per chunk the weights 0..3 and 4..7 are gathered
+// exactly into two integers, hi = sum_{w<4} P_w 2^(B (3 - w)) and
+// lo = sum_{w>=4} P_w 2^(B (7 - w)) (below 2^46 each), and each enters the
+// FP64 sum through one fused multiply-add by its power of two.
+__global__ void k_oz_combine(const float *__restrict__ P, int c0, int nc, int nchunk, int R, int nd,
+                             const int *__restrict__ ea, const int *__restrict__ eb, double *__restrict__ O,
+                             int ldo, int accumulate) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)R * nd) return;
     const int r = (int)(idx / nd), d = (int)(idx - (long long)r * nd);
@@ -125,10 +149,14 @@ __global__ void k_oz_combine(const float *__restrict__ P, int npair, PairArg pr,
     for (int c = 0; c < nc; ++c) {
         const int base = __ldg(ea + (size_t)r * nchunk + c0 + c) + __ldg(eb + (size_t)d * nchunk + c0 + c) -
                          2 * OZ_S * OZ_B + OZ_B * (2 * OZ_S - 2);
-        for (int u = 0; u < npair; ++u) {
-            const float v = P[((size_t)u * nc + c) * plane + idx];
-            s += ldexp((double)v, base - OZ_B * (pr.a[u] + pr.b[u]));
-        }
+        long long hi = 0, lo = 0;
+#pragma unroll
+        for (int w = 0; w < OZ_S / 2; ++w) hi = hi * (1 << OZ_B) + __float2ll_rn(P[((size_t)w * nc + c) * plane + idx]);
+#pragma unroll
+        for (int w = OZ_S / 2; w < OZ_S; ++w)
+            lo = lo * (1 << OZ_B) + __float2ll_rn(P[((size_t)w * nc + c) * plane + idx]);
+        s = fma((double)hi, pow2(base - OZ_B * (OZ_S / 2 - 1)), s);
+        s = fma((double)lo, pow2(base - OZ_B * (OZ_S - 1)), s);
     }
     O[(size_t)r * ldo + d] = s;
 }
@@ -233,22 +261,23 @@ int oz_run(const fk_table *t, const TcPack &pk, const int *pe, int kchunk, const
     CUtensorMap mA;
     int rc = tc_map_bf16(&mA, Aoz, pk.ktot_pad, (long long)OZ_S * R_pad, 128);
     if (rc) return rc;
-    const Pairs pr = oz_pairs();
-    PairArg pa;
-    std::copy(pr.a, pr.a + pr.n, pa.a);
-    std::copy(pr.b, pr.b + pr.n, pa.b);
-    // chunks per launch: the partial tiles of all pairs within OZ_PART_BYTES
-    const size_t per_chunk = (size_t)pr.n * R * nd_out * sizeof(float);
+    // chunks per launch: the 8 weight partials of a chunk within OZ_PART_BYTES
+    const size_t per_chunk = (size_t)OZ_S * R * nd_out * sizeof(float);
     const int cb = (int)std::max<size_t>(1, std::min<size_t>(nchunk, OZ_PART_BYTES / std::max<size_t>(per_chunk, 1)));
     float *P = nullptr;
-    FK_CUDA(scr.get(&P, (size_t)cb * pr.n * R * nd_out));
+    FK_CUDA(scr.get(&P, (size_t)cb * OZ_S * R * nd_out));
     for (int c0 = 0; c0 < nchunk; c0 += cb) {
         const int nc = std::min(cb, nchunk - c0);
-        rc = tc_slice_pairs(t, pk, mA, R, nd_out, kchunk, c0, nc, pr.n, pr.a, pr.b, P, s);
-        if (rc) return rc;
+        for (int w = 0; w < OZ_S; ++w) {  // one launch per weight: its w + 1 pairs in one accumulator
+            uint8_t pa[OZ_S], pb[OZ_S];
+            const int npc = weight_pairs(w, pa, pb);
+            rc = tc_slice_pairs(t, pk, mA, R, nd_out, kchunk, c0, nc, 1, npc, pa, pb,
+                                P + (size_t)w * nc * R * nd_out, s);
+            if (rc) return rc;
+        }
         const long long n = (long long)R * nd_out;
-        k_oz_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, pr.n, pa, c0, nc, nchunk, R, nd_out, ea, pe, O,
-                                                                 ldo, accumulate || c0 > 0);
+        k_oz_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, c0, nc, nchunk, R, nd_out, ea, pe, O, ldo,
+                                                                 accumulate || c0 > 0);
         count_launch();
         FK_CUDA(cudaGetLastError());
     }

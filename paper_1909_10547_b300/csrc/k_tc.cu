@@ -319,6 +319,10 @@ struct TcParams {
     int npair, a_rows, b_rows;
     uint8_t pa[64], pb[64];
     int kbase;  // K element where split 0 starts
+    // npc > 1: a work item accumulates npc operand pairs in one accumulator;
+    // its stages run pair j = q / spc over the split's K (stage q % spc), and
+    // pair u of the launch stands for pairs pa/pb[u * npc + j]
+    int npc, spc;
 };
 
 // Epilogue modes of the tensor-core kernel.
@@ -447,11 +451,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int w = w_first; w < w_count && ok; w += w_step) {
             int rt, nt, sp, pr;
             tile_of(w, rt, nt, sp, pr);
-            const int brow = p.pb[pr] * p.b_rows + nt * p.n_rows + (int)rank * b_rows;
-            const int arow = p.pa[pr] * p.a_rows + rt * TC_M;
             const int koff = p.kbase + sp * p.kspl;  // the split's first K element
             int pg = 0;  // next group whose first stage is still to be loaded
             for (int q = 0; q < p.nchunks; ++q, ++it) {
+                // the operand pair and K stage of this stage (one pair unless npc > 1)
+                const int j = p.npc > 1 ? q / p.spc : 0;
+                const int qk = q - j * (p.npc > 1 ? p.spc : 0);
+                const int u = p.npc > 1 ? pr * p.npc + j : pr;
+                const int brow = p.pb[u] * p.b_rows + nt * p.n_rows + (int)rank * b_rows;
+                const int arow = p.pa[u] * p.a_rows + rt * TC_M;
                 const int s = it % S;
                 if (leader) {
                     // the accumulator of every group starting in this stage
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (leader) mbar_expect_tx(full(s), 2 * stage_bytes);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
-                        const int x = koff + q * T::KCS + a * T::KC;
+                        const int x = koff + qk * T::KCS + a * T::KC;
                         tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, arow);
                         tma_load_2d_pair(st + offB + a * b_bytes, &mapB, fb, x, brow);
                         if (T::X3) {
@@ -488,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(full(s), stage_bytes);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
-                        const int x = koff + q * T::KCS + a * T::KC;
+                        const int x = koff + qk * T::KCS + a * T::KC;
                         tma_load_2d(st + a * a_bytes, &mapA, full(s), x, arow);
                         tma_load_2d(st + offB + a * b_bytes, &mapB, full(s), x, brow);
                         if (T::X3) {
@@ -1763,15 +1771,17 @@ int tc_map_bf16(CUtensorMap *m, const void *ptr, long long cols, long long rows,
     return make_map(m, ptr, 2, cols, rows, box_rows);
 }
 
-// The BF16 products of npair (A slice, B slice) pairs over K chunks c0 ..
-// c0 + nsplit - 1 of kchunk elements (a multiple of 128): A map over [S * R_pad][ktot_pad]
-// (slice u's rows start at pa[u] * R_pad), B the pack's stacked slices
-// (pb[u] * ntile_n * n_rows); partial tile (u, sp) lands at
-// P + (u * nsplit + sp) * R * nd_out, [R][nd_out].  The last chunk may run
-// past the operands' K, which the tensor maps read as zeros.
+// The BF16 products of npair groups of npc (A slice, B slice) pairs over K
+// chunks c0 .. c0 + nsplit - 1 of kchunk elements (a multiple of 128): A map
+// over [S * R_pad][ktot_pad] (slice p's rows start at p * R_pad), B the pack's
+// stacked slices (q * ntile_n * n_rows); group u sums its pairs
+// (pa, pb)[u * npc + j] in one accumulator, and its partial tile for chunk
+// c0 + sp lands at P + (u * nsplit + sp) * R * nd_out, [R][nd_out].  The last
+// chunk may run past the operands' K, which the tensor maps read as zeros.
 int tc_slice_pairs(const fk_table *t, const TcPack &pk, const CUtensorMap &mA, int R, int nd_out, int kchunk,
-                   int c0, int nsplit, int npair, const uint8_t *pa, const uint8_t *pb, float *P, cudaStream_t s) {
-    if (npair < 1 || npair > 64 || kchunk % Tr<FK_BF16>::KCS)
+                   int c0, int nsplit, int npair, int npc, const uint8_t *pa, const uint8_t *pb, float *P,
+                   cudaStream_t s) {
+    if (npair < 1 || npc < 1 || npair * npc > 64 || kchunk % Tr<FK_BF16>::KCS)
         return fail(FK_EINVAL, "tc_slice_pairs: bad pair count or chunk");
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     TcParams p{};
@@ -1781,13 +1791,15 @@ int tc_slice_pairs(const fk_table *t, const TcPack &pk, const CUtensorMap &mA, i
     p.nbl = pk.n_rows <= 128 ? 2 : 1;
     p.ngroups = 1;
     p.kbeg[0] = 0;
-    p.kend[0] = kchunk;
     p.kspl = kchunk;
     p.kbase = c0 * kchunk;
-    p.nchunks = kchunk / Tr<FK_BF16>::KCS;
+    p.spc = kchunk / Tr<FK_BF16>::KCS;
+    p.npc = npc;
+    p.nchunks = npc * p.spc;  // stages per work item: npc pairs over one chunk
+    p.kend[0] = npc * kchunk;
     p.nsplit = nsplit;
     p.npair = npair;
-    for (int u = 0; u < npair; ++u) {
+    for (int u = 0; u < npair * npc; ++u) {
         p.pa[u] = pa[u];
         p.pb[u] = pb[u];
     }

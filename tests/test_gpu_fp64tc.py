@@ -8,7 +8,7 @@ oracle every result meets the FP64 contract, 1e-12 of S = sum |terms|, on
 the configuration tables (config 0 DIS, config 1 hadronic, the DIS and
 hadronic tables of the global set, Table 3's base table); with values spread
 over 60 orders of magnitude in a row the error stays within the scheme's own
-bound (per K chunk, 2^-48 K_c times the rows' largest values); a replica's
+bound (per K chunk of 512, 2^-48 K_c times the rows' largest values); a replica's
 result does not depend on R; the fit step in this mode matches the oracle
 chain at 1e-12.
 """
@@ -49,7 +49,7 @@ def abs_table(t):
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (37, 1000, 130), (300, 2100, 3), (8, 4099, 257)])
 def test_dense_exact_small_integers(shape):
-    """(ndata, K, R): K over several 1024 chunks (ragged last chunk), two data
+    """(ndata, K, R): K over several 512 chunks (ragged last chunk), two data
     tiles, paired and odd replica tiles."""
     nd, K, R = shape
     rng = np.random.default_rng(sum(shape))
@@ -124,7 +124,7 @@ def test_table3_dense_against_oracle():
 def test_wide_dynamic_range_within_a_row():
     """Values over 60 orders of magnitude in one row.  The slices hold each
     value to within 2^-55 of the largest |value| of its row in its K chunk
-    (chunks of 1024), and each of the 28 dropped digit products is below
+    (chunks of 512), and each of the 28 dropped digit products is below
     2^-56 of the chunk's largest one, so per chunk the error is below
     K_c 2^-48 max|A_r| max|B_d|: the bound checked here.  (Relative to S this
     input is far outside the contract's reach: its largest elements of A and
@@ -137,8 +137,8 @@ def test_wide_dynamic_range_within_a_row():
     tab = fk.Table.dense(fkd, precs=(P,))
     O = fk.dense_conv(tab, torch.tensor(L, device="cuda"), P).cpu().numpy()
     bound = np.zeros((R, nd))
-    for c0 in range(0, K, 1024):
-        sl = slice(c0, min(K, c0 + 1024))
+    for c0 in range(0, K, 512):
+        sl = slice(c0, min(K, c0 + 512))
         kc = sl.stop - sl.start
         bound += kc * 2.0 ** -48 * np.abs(L[:, sl]).max(axis=1)[:, None] * np.abs(fkd[:, sl]).max(axis=1)[None, :]
     assert np.all(np.abs(O - O_ref) <= bound)

@@ -400,7 +400,7 @@ def roof_entry(prec, byts, flops, ms, kernel, traffic=None):
     return r
 
 
-def kernel_lines(args, stress_tab=None, stress_t=None):
+def kernel_lines(args, stress_tab=None, stress_t=None, stress_oz=None):
     """Kernel-level lines: each one call of one path, timed on its own with
     its own roofline.  Stress table (2000 x 196 channels x 50 x 50; resident
     tables far larger than L2): R = 1 FP32 streaming and R = 1000 BF16 on the
@@ -444,9 +444,20 @@ def kernel_lines(args, stress_tab=None, stress_t=None):
                  roof_entry(prec, elems * ESZ[prec], 2.0 * elems * R, ms,
                             "k_tc (whole call: operand packing + tcgen05 kernel)", traffic_of("k_tc", prec, nd, R)))
         del FR, OR
+        if stress_oz is not None:
+            R = 100
+            F64 = torch.tensor(W.pdf_replicas(W.xgrid(50, 1e-7), W.pdf_params(np.random.default_rng(1)), R,
+                                              np.random.default_rng(2)), device="cuda")
+            O64 = torch.empty((R, nd), dtype=torch.float64, device="cuda")
+            ms = time_calls(lambda: fk.conv(stress_oz, F64, "fp64tc", out=O64), 3)
+            line("stress table, R=100, FP64 results on the tensor cores (fp64tc)", "fp64tc", nd * R, ms,
+                 roof_entry("fp64tc", elems * 8, 2.0 * elems * R, ms,
+                            "k_oz_slice + k_tc digit pairs + k_oz_combine (whole call)"),
+                 fp64_pipe_ms_reference="249 ms (k_fac FP64, bench.py --case stress --prec fp64 --replicas 100)")
+            del F64, O64
     # configs 1-2 table
     t1, F1h = W.config1(R=512)
-    tab1 = fk.Table.from_workload(t1, precs=("fp32", "bf16", "bf16x3", "tf32"))
+    tab1 = fk.Table.from_workload(t1, precs=("fp64", "fp32", "bf16", "bf16x3", "tf32", "fp64tc"))
     e1 = t1.fk.size
     nd1 = t1.ndata
     Fa = torch.tensor(F1h, dtype=torch.float32, device="cuda")
@@ -463,6 +474,13 @@ def kernel_lines(args, stress_tab=None, stress_t=None):
             line(f"config 2: config 1 table, R=512, {prec} tensor cores, {'cold L2' if cold else 'warm L2'}", prec,
                  nd1 * 512, ms, roof_entry(prec, e1 * ESZ[prec], 2.0 * e1 * 512, ms,
                                            "k_tc (whole call: operand packing + tcgen05 kernel)"))
+    # config 1 at R = 100 with FP64 results: the FP64 pipe against the tensor cores
+    F100 = torch.tensor(F1h[:100], device="cuda")
+    O100 = torch.empty((100, nd1), dtype=torch.float64, device="cuda")
+    for prec, kern in (("fp64", "k_fac (FP64 pipe)"), ("fp64tc", "k_oz_slice + k_tc digit pairs + k_oz_combine")):
+        ms = time_calls(lambda: fk.conv(tab1, F100, prec, out=O100), steps)
+        line(f"config 1: R=100, FP64 results, {prec}", prec, nd1 * 100, ms,
+             roof_entry(prec, e1 * 8, 2.0 * e1 * 100, ms, kern))
     del tab1
     # config 0 (DIS, FP64, R = 1) and 4096 of its tables stacked
     t0, F0h = W.config0()
@@ -499,10 +517,24 @@ def kernel_lines(args, stress_tab=None, stress_t=None):
              roof_entry("fp32", 8 * K * 4 + K * 4, 2.0 * 8 * K, ms, "k_stream<DENSE> + k_reduce_parts"),
              paper_seconds={10 ** 6: 5.0e-3, 10 ** 7: 5.7e-2}[K])
         del tabd, L
+    # Table 3's last line (2000 x 35721 x 2000) with FP64 results on the tensor cores
+    t3, F3 = W.table3(2000, 2000)
+    K3 = t3.fk[0].size
+    tab3 = fk.Table.dense(t3.fk.reshape(2000, K3), precs=("fp64tc",))
+    ht3 = fk.Table.from_workload(t3, precs=("fp64",))
+    del t3
+    L3 = fk.luminosity(ht3, torch.tensor(F3, device="cuda"), "fp64")
+    O3 = torch.empty((2000, 2000), dtype=torch.float64, device="cuda")
+    ms = time_calls(lambda: fk.dense_conv(tab3, L3, "fp64tc", out=O3), 3)
+    line("Table 3 line 147: dense 2000 x 35721 . PDF [35721 x 2000], FP64 results on the tensor cores", "fp64tc",
+         2000 * 2000, ms, roof_entry("fp64tc", 2000 * K3 * 8, 2.0 * 2000 * K3 * 2000, ms,
+                                     "k_oz_slice + k_tc digit pairs + k_oz_combine"),
+         paper_seconds=1.38, fp64_pipe_ms_reference="254 ms (k_tile FP64, bench.py --case dense --prec fp64)")
+    del tab3, ht3, L3, O3
     return out
 
 
-def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0):
+def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0, plain_prec=None):
     """The served mixed workload, bounded: n requests with Poisson arrivals at
     `rate` over the global-set tables (+ the stress table), R from
     {1, 10, 100, 1000}, resident tables, 150 GB budget.  Reports open-loop
@@ -540,7 +572,7 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0):
         seen.setdefault((w, F.shape[0]), (w, F, p))
     for w, F, p in seen.values():
         srv.wait(srv.submit(ids[w], F, p), 600000)
-        fk.conv(alltabs[w], torch.from_numpy(F).to("cuda"), p).cpu()
+        fk.conv(alltabs[w], torch.from_numpy(F).to("cuda"), plain_prec or p).cpu()
     tickets = [None] * n
     t_sub = np.zeros(n)
     t_done = np.zeros(n)
@@ -587,10 +619,11 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0):
     for w, F, p in work:
         a = time.perf_counter()
         Fd = torch.from_numpy(F).to("cuda")
-        fk.conv(alltabs[w], Fd, p).cpu()
+        fk.conv(alltabs[w], Fd, plain_prec or p).cpu()
         plain.append((time.perf_counter() - a) * 1e3)
     plain_span = time.perf_counter() - t1
-    return {"requests": n, "offered_rate": rate, "tables": len(alltabs),
+    return {"requests": n, "offered_rate": rate, "tables": len(alltabs), "mode": allprec[0],
+            "per_request_mode": plain_prec or allprec[0],
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "achieved_rate": n / span, "open_loop_value": units / span,
             "saturation_value": units / sat, "unit": UNIT, "launches": st["launches"],
@@ -1238,6 +1271,26 @@ def main():
                     "h2d_bytes_per_step": inner * F_host.numel() * F_host.element_size(),
                     "d2h_bytes_per_step": inner * (chi2_host.numel() * 8 + gF_host.numel() * gF_host.element_size())},
             "gpu_launches": launches * args.steps * inner, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the served mixes first (the server's threads then meet a quiet
+        # host), then the kernel-level lines
+        from paper_1909_10547_b300 import workloads as W
+        try:
+            st = W.stress_table()
+            stress_tab = fk.Table.from_workload(st, precs=("fp32", "bf16", "bf16x3"))
+            line["serve"] = serve_block(args, g, fit.tabs, fit.tprec, stress_tab)
+            # FP64-contract serving: FP64 results on the tensor cores, served,
+            # against the plain FP64 path one request at a time (global set)
+            tabs64 = [fk.Table.from_workload(t, precs=("fp64", "fp64tc")) for t in g.tables]
+            line["serve_fp64"] = serve_block(args, g, tabs64, ["fp64tc"] * len(tabs64), None, n=400,
+                                             plain_prec="fp64")
+            del tabs64
+            stress_oz = fk.Table.from_workload(st, precs=("fp64tc",))
+            line["kernels"] = kernel_lines(args, stress_tab, st, stress_oz)
+            del st, stress_oz, stress_tab
+            torch.cuda.synchronize()
+        except Exception as exc:  # the headline stands; say what failed
+            line["extras_error"] = f"{type(exc).__name__}: {exc}"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         D_parts = np.split(D, np.cumsum([t.ndata for t in g.tables])[:-1])
         cb = cpu_baseline(g, cov.blocks, D_parts)
@@ -1257,18 +1310,6 @@ def main():
                             "replicas_compared": nr, "mode": args.prec,
                             "chi2_max_rel_err": float(np.max(np.abs(chi / cb["chi2"] - 1))),
                             "grad_max_err_rel_to_max": float(np.abs(gF - cb["gF"]).max() / np.abs(cb["gF"]).max())}
-    if rank == 0 and world == 1 and not args.no_extras:
-        from paper_1909_10547_b300 import workloads as W
-        try:
-            st = W.stress_table()
-            stress_tab = fk.Table.from_workload(st, precs=("fp32", "bf16", "bf16x3"))
-            line["kernels"] = kernel_lines(args, stress_tab, st)
-            del st
-            torch.cuda.synchronize()
-            line["serve"] = serve_block(args, g, fit.tabs, fit.tprec, stress_tab)
-            del stress_tab
-        except Exception as exc:  # the headline stands; say what failed
-            line["extras_error"] = f"{type(exc).__name__}: {exc}"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -349,7 +349,7 @@ int fk_serve_add_table(fk_server *s, fk_table *t, int *table_id) {
 
 int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int prec, uint64_t *ticket) {
     if (!s || !F_host || !ticket || R < 1) return fail(FK_EINVAL, "fk_serve_submit: bad argument");
-    if (prec < FK_FP64 || prec > FK_TF32) return fail(FK_EINVAL, "fk_serve_submit: unknown precision");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "fk_serve_submit: unknown precision");
     fk_table *t;
     {
         std::lock_guard<std::mutex> l(s->mu);

@@ -59,14 +59,19 @@ def parse():
     ap.add_argument("--waves", type=int, default=1, help="fit case: forward waves of the pipelined step")
     ap.add_argument("--streams", type=int, default=0,
                     help="fit case: streams the tables are spread over (0: one per table)")
-    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent", "dense", "peaks"],
+    ap.add_argument("--case", default="fit", choices=["fit", "stress", "serve", "descent", "dense", "peaks", "dis"],
                     help="fit: the fit step (default, the headline line); stress: one convolution "
                          "of the hadronic stress table (2000 x 196 channels x 50 x 50) for kernel rooflines; "
                          "serve: the served mixed workload (Poisson arrivals over 41 resident tables); "
                          "descent: Adam on the PDF parameters of every replica, iterations of the fit; "
                          "dense: the paper's Table 3 product FK[ndata x 35721] . PDF[35721 x R] "
                          "(--ndata, --replicas; default 2000 x 2000); "
-                         "peaks: measures the TF32 (cuBLAS), FP32 and FP64 (multiply-add loops) peaks")
+                         "peaks: measures the TF32 (cuBLAS), FP32 and FP64 (multiply-add loops) peaks; "
+                         "dis: the config-0 DIS table (64 x 9 x 40), --stack copies stacked along the data "
+                         "points, --replicas (default 1), --prec (default fp64 here)")
+    ap.add_argument("--stack", type=int, default=1, help="dis case: config-0 tables stacked")
+    ap.add_argument("--kdense", type=int, default=0,
+                    help="dense case: a seeded random table [ndata][kdense] instead of Table 3's base table")
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
@@ -497,13 +502,15 @@ def kernel_lines(args, stress_tab=None, stress_t=None, stress_oz=None):
     nb = 4096
     rng = np.random.default_rng(10547)
     big = np.abs(rng.standard_normal((nb * t0.ndata, len(t0.flav), t0.nx))) * (W.xgrid(t0.nx, 1e-7) ** 0.3)[None, None, :]
-    tabb = fk.Table.dis(big, t0.flav, None, t0.nx, precs=("fp64",))
+    tabb = fk.Table.dis(big, t0.flav, None, t0.nx, precs=("fp64", "fp32"))
     del big
-    Ob = torch.empty((1, nb * t0.ndata), dtype=torch.float64, device="cuda")
-    ms = time_calls(lambda: fk.dis_conv(tabb, F0, "fp64", out=Ob), steps)
     ub = used0 * nb
-    line("config 0 x 4096: 4096 DIS tables 64x9x40 stacked (262144 points), R=1, FP64", "fp64", nb * t0.ndata, ms,
-         roof_entry("fp64", ub * 8, 2.0 * ub, ms, "k_stream<DIS> + k_reduce_parts"))
+    F0s = F0.float()
+    for prec, Fx in (("fp64", F0), ("fp32", F0s)):
+        Ob = torch.empty((1, nb * t0.ndata), dtype=Fx.dtype, device="cuda")
+        ms = time_calls(lambda: fk.dis_conv(tabb, Fx, prec, out=Ob), steps)
+        line(f"config 0 x 4096: 4096 DIS tables 64x9x40 stacked (262144 points), R=1, {prec}", prec,
+             nb * t0.ndata, ms, roof_entry(prec, ub * ESZ[prec], 2.0 * ub, ms, "k_stream<DIS> + k_reduce_parts"))
     del tabb
     # Table 3 rows with R = 1: ndata = 8, K = 1e6, 1e7
     for K in (10 ** 6, 10 ** 7):
@@ -839,16 +846,21 @@ def run_dense(args):
     from paper_1909_10547_b300 import workloads as W
     R = args.replicas or 2000
     nd = args.ndata
-    t, F = W.table3(nd, R)
-    K = t.fk[0].size
     prec = args.prec
     f64 = prec in ("fp64", "fp64tc")
     io = torch.float64 if f64 else torch.float32
-    ht = fk.Table.from_workload(t, precs=("fp64" if f64 else "fp32",))
-    tab = fk.Table.dense(t.fk.reshape(nd, K), precs=(prec,))
-    del t
-    Fd = torch.tensor(F, dtype=io, device="cuda")
-    L = fk.luminosity(ht, Fd, "fp64" if f64 else "fp32")
+    if args.kdense:
+        K = args.kdense
+        tab = fk.Table.dense(np.random.default_rng(K).standard_normal((nd, K)), precs=(prec,))
+        L = torch.rand((R, K), dtype=io, device="cuda")
+    else:
+        t, F = W.table3(nd, R)
+        K = t.fk[0].size
+        ht = fk.Table.from_workload(t, precs=("fp64" if f64 else "fp32",))
+        tab = fk.Table.dense(t.fk.reshape(nd, K), precs=(prec,))
+        del t
+        Fd = torch.tensor(F, dtype=io, device="cuda")
+        L = fk.luminosity(ht, Fd, "fp64" if f64 else "fp32")
     O = fk.dense_conv(tab, L, prec)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -974,6 +986,40 @@ def run_stress(args):
             "config": {"workload": name, "l2": "table larger than L2" if byts > 126e6 else
                        "table fits in L2 (warm: replayed back to back)", "graphs": True},
             "roofline": roof, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_dis(args):
+    """The DIS convolution of config 0 (64 data points, 9 of 14 flavours, 40 x
+    points, one PDF), --stack copies of the table stacked along the data
+    points, timed over graph replays (back to back)."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    from paper_1909_10547_b300 import workloads as W
+    prec = args.prec
+    R = args.replicas or 1
+    t0, _ = W.config0()
+    x = W.xgrid(40, 1e-7)
+    rng = np.random.default_rng(5)
+    F = W.pdf_replicas(x, W.pdf_params(rng), R, rng if R > 1 else None)
+    comp = t0.compact()
+    if args.stack > 1:
+        comp = np.abs(np.random.default_rng(10547).standard_normal((args.stack * t0.ndata,) + comp.shape[1:])) * \
+            (x ** 0.3)[None, None, :]
+    tab = fk.Table.dis(comp, t0.flav, None, 40, precs=(prec,))
+    nd = comp.shape[0]
+    used = comp.size
+    del comp
+    dt = torch.float64 if prec in ("fp64", "fp64tc") else torch.float32
+    Fd = torch.tensor(F, dtype=dt, device="cuda")
+    O = torch.empty((R, nd), dtype=dt, device="cuda")
+    ms = time_calls(lambda: fk.dis_conv(tab, Fd, prec, out=O), args.steps)
+    roof = roof_entry(prec, used * ESZ[prec], 2.0 * used * R, ms, "DIS convolution call")
+    line = {"metric": METRIC, "value": nd * R / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"DIS 64 x 9 x 40 (config 0) x {args.stack} stacked, R={R}", "graphs": True},
+            "roofline": roof, "latency_us": ms * 1e3}
     print(json.dumps(line), flush=True)
 
 
@@ -1170,6 +1216,9 @@ def main():
         return
     if args.case == "peaks":
         run_peaks(args)
+        return
+    if args.case == "dis":
+        run_dis(args)
         return
     rank, world, dist = dist_init(args.gpus)
     if args.impl == "reference":

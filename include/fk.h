@@ -61,7 +61,8 @@ enum {
     FK_ETIMEDOUT = 5,   /* a bounded wait ran out */
     FK_ECUDA = 6,       /* a CUDA runtime call or kernel launch failed */
     FK_ENOTFOUND = 7,   /* unknown ticket or table id */
-    FK_EUNSUPPORTED = 8 /* precision not stored in this table, or not offered */
+    FK_EUNSUPPORTED = 8, /* precision not stored in this table, or not offered */
+    FK_ECANCELED = 9    /* served request cancelled (or its server destroyed first) */
 };
 
 /* Arithmetic modes.  FP64 and FP32 read and write buffers of that type.  The
@@ -119,6 +120,22 @@ int fk_device_status(int reset);
  * Returns FK_OK if the flag was raised (and clears it; a flag set before the
  * call is cleared too), FK_ECUDA otherwise.  The device stays usable. */
 int fk_wait_selftest(int limit_us);
+
+/*
+ * Debug builds.  libfk_debug.so (python -m paper_1909_10547_b300.build
+ * --debug; loaded by the Python binding when FK_DEBUG=1) compiles index
+ * checks into the kernels: a check that fails records its code and the
+ * offending index in a device word and skips the access instead of touching
+ * memory out of range, and every per-call scratch buffer carries guard bytes
+ * that are verified when the call's scratch is released (code 90).
+ * fk_debug_status reads the first failed check since the last reset (code 0:
+ * none) and clears it if reset != 0; fk_debug_selftest launches one check
+ * that must fail (index 4 of a 4-element buffer, code 99) and verifies it is
+ * reported.  Both return FK_EUNSUPPORTED in a release build.  They have no
+ * counterpart in the paper.
+ */
+int fk_debug_status(int reset, int *code, long long *index);
+int fk_debug_selftest(void);
 
 /* ---------------------------------------------------------------- tables */
 
@@ -389,7 +406,10 @@ int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int p
  * status; otherwise sets *done = 0 and returns FK_EPENDING.
  */
 int fk_serve_poll(fk_server *s, uint64_t ticket, void *O_host, int *done);
-/* As fk_serve_poll, but waits up to timeout_ms (FK_ETIMEDOUT after that). */
+/* As fk_serve_poll, but waits up to timeout_ms; FK_EPENDING if the request
+ * has not finished by then (the ticket stays valid).  A request that finished
+ * with a failure returns that failure's status (FK_ETIMEDOUT: its completion
+ * was lost, see below). */
 int fk_serve_wait(fk_server *s, uint64_t ticket, void *O_host, int timeout_ms);
 /*
  * Counters since creation: completed requests, sum of ndata*R over them,
@@ -398,7 +418,38 @@ int fk_serve_wait(fk_server *s, uint64_t ticket, void *O_host, int timeout_ms);
  */
 int fk_serve_stats(const fk_server *s, uint64_t *completed, uint64_t *datapoint_replicas,
                    uint64_t *launches, size_t *peak_bytes, int *queued);
-/* Stops the scheduler after the requests in flight finish; frees requests. */
+/*
+ * Cancels a request: one not started yet is removed from the queue; one
+ * running finishes but its result is discarded.  Either way its poll/wait
+ * then returns FK_ECANCELED (a request already finished keeps its result).
+ * FK_ENOTFOUND for an unknown ticket.
+ */
+int fk_serve_cancel(fk_server *s, uint64_t ticket);
+
+/*
+ * Failure detection.  Every failure of a served request ends in its own
+ * status at poll/wait, and nothing waits forever:
+ *  - a failed pinned staging allocation: fk_serve_submit returns FK_ENOMEM;
+ *  - a failed device allocation for a batch: its requests end FK_ENOMEM;
+ *  - a failed convolution launch: its requests end FK_ECUDA;
+ *  - a lost completion message (the batch's work finished but the host was
+ *    never told): once the batch's work has finished and 200 ms have passed,
+ *    its requests end FK_ETIMEDOUT and its budget is returned;
+ *  - fk_serve_destroy with requests queued: they end FK_ECANCELED.
+ * fk_serve_inject arms `count` occurrences of one host-side fault, so that
+ * these paths can be tested without any fault on the GPU: FK_FAULT_PINNED
+ * (the next submits' pinned allocation fails), FK_FAULT_DEVICE (the next
+ * batches' device allocation fails), FK_FAULT_LAUNCH (the next batches'
+ * convolution launch fails), FK_FAULT_DROP (the next batches' completion
+ * message is lost).  The environment variable FK_FAULT="kind:count,..."
+ * (kinds pinned, device, launch, drop) arms the same at fk_serve_create.
+ * The paper has no counterpart (it describes no serving).
+ */
+enum { FK_FAULT_PINNED = 1, FK_FAULT_DEVICE = 2, FK_FAULT_LAUNCH = 3, FK_FAULT_DROP = 4 };
+int fk_serve_inject(fk_server *s, int fault, int count);
+
+/* Stops the scheduler: requests still queued end FK_ECANCELED, the ones in
+ * flight finish; frees the requests and the server. */
 int fk_serve_destroy(fk_server *s);
 
 #ifdef __cplusplus

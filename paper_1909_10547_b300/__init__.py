@@ -316,12 +316,24 @@ class Server:
     def wait(self, ticket: int, timeout_ms: int = 60000) -> np.ndarray:
         O = self._out(ticket)
         rc = _lib.load().fk_serve_wait(self._h, ctypes.c_uint64(ticket), _p(O), int(timeout_ms))
-        if rc == _lib.FK_ETIMEDOUT:
+        if rc == _lib.FK_EPENDING:
             raise TimeoutError(f"ticket {ticket} still running after {timeout_ms} ms")
         self._meta.pop(ticket, None)
         if rc != 0:
             raise FKError("fk_serve_wait", rc, _lib.load())
         return O
+
+    def cancel(self, ticket: int):
+        """Cancels a request (fk_serve_cancel): its poll/wait then raises
+        FKError with FK_ECANCELED, unless it had finished already."""
+        _lib.call("fk_serve_cancel", self._h, ctypes.c_uint64(ticket))
+
+    def inject(self, fault: str, count: int = 1):
+        """Arms `count` host-side faults (fk_serve_inject): "pinned", "device",
+        "launch" or "drop" (a lost completion message)."""
+        kind = {"pinned": _lib.FK_FAULT_PINNED, "device": _lib.FK_FAULT_DEVICE, "launch": _lib.FK_FAULT_LAUNCH,
+                "drop": _lib.FK_FAULT_DROP}[fault]
+        _lib.call("fk_serve_inject", self._h, kind, int(count))
 
     def stats(self) -> dict:
         c, d, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

@@ -17,6 +17,8 @@ SIGNATURES = {
     "fk_version": [],
     "fk_device_status": [I],
     "fk_wait_selftest": [I],
+    "fk_debug_status": [I, P, P],
+    "fk_debug_selftest": [],
     "fk_table_create_dis": [P, I, P, I, I, P, I, U, PP],
     "fk_table_create_had": [P, I, P, P, I, I, P, I, U, PP],
     "fk_table_destroy": [P],
@@ -44,6 +46,8 @@ SIGNATURES = {
     "fk_serve_poll": [P, U64, P, P],
     "fk_serve_wait": [P, U64, P, I],
     "fk_serve_stats": [P, P, P, P, P, P],
+    "fk_serve_cancel": [P, U64],
+    "fk_serve_inject": [P, I, I],
     "fk_serve_destroy": [P],
 }
 U64_FUNCS = {"fk_kernel_launches": []}
@@ -53,24 +57,31 @@ _lib = None
 _lock = threading.Lock()
 
 
+def debug() -> bool:
+    """True when FK_DEBUG=1: the debug build libfk_debug.so is loaded."""
+    return os.environ.get("FK_DEBUG") == "1"
+
+
 def path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug() else _build.LIB
 
 
 def load():
-    """Loads libfk.so (building it first if the sources are newer and nvcc is
-    present).  Raises if the library cannot be loaded: there is no fallback."""
+    """Loads libfk.so (libfk_debug.so when FK_DEBUG=1), building it first if
+    the sources are newer and nvcc is present.  Raises if the library cannot
+    be loaded: there is no fallback."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if not _build.up_to_date():
+        dbg = debug()
+        if not _build.up_to_date(dbg):
             try:
-                _build.build()
+                _build.build(debug=dbg)
             except (OSError, RuntimeError) as e:
-                if not os.path.exists(_build.LIB):
-                    raise RuntimeError(f"libfk.so is missing and could not be built: {e}") from e
-        lib = ctypes.CDLL(_build.LIB)
+                if not os.path.exists(path()):
+                    raise RuntimeError(f"{os.path.basename(path())} is missing and could not be built: {e}") from e
+        lib = ctypes.CDLL(path())
         for name, args in SIGNATURES.items():
             f = getattr(lib, name)
             f.argtypes = args
@@ -105,7 +116,8 @@ def call(name, *args):
 
 # status codes and precisions (include/fk.h)
 FK_OK, FK_EINVAL, FK_ENOMEM, FK_EBUDGET, FK_EPENDING, FK_ETIMEDOUT, FK_ECUDA, FK_ENOTFOUND, \
-    FK_EUNSUPPORTED = range(9)
+    FK_EUNSUPPORTED, FK_ECANCELED = range(10)
+FK_FAULT_PINNED, FK_FAULT_DEVICE, FK_FAULT_LAUNCH, FK_FAULT_DROP = range(1, 5)
 FK_FP64, FK_FP32, FK_BF16, FK_BF16X3, FK_TF32, FK_FP64_TC = range(6)
 PRECS = {"fp64": FK_FP64, "fp32": FK_FP32, "bf16": FK_BF16, "bf16x3": FK_BF16X3, "tf32": FK_TF32,
          "fp64tc": FK_FP64_TC}

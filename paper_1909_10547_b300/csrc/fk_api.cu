@@ -215,7 +215,18 @@ int check_conv(const fk_table *t, int kind, const void *F, int R, const void *O,
     return FK_OK;
 }
 
+#ifdef FK_DEBUG
+// Writes buf[idx] through a debug check: with idx out of range the check
+// records it and the write is skipped.  Launched only in debug builds.
+__global__ void k_dbg_selftest(int *buf, int n, int idx) {
+    if (FK_DBG(idx >= 0 && idx < n, 99, idx)) buf[idx] = 1;
+}
+#endif
+
 }  // namespace
+
+FK_DBG_READER(dbg_api)
+
 }  // namespace fk
 
 using namespace fk;
@@ -233,6 +244,7 @@ const char *fk_strerror(int s) {
         case FK_ECUDA: return "CUDA error";
         case FK_ENOTFOUND: return "not found";
         case FK_EUNSUPPORTED: return "unsupported precision or table kind";
+        case FK_ECANCELED: return "request cancelled";
         default: return "unknown status";
     }
 }
@@ -242,6 +254,50 @@ const char *fk_last_error_message(void) { return g_last_error.c_str(); }
 int fk_version(void) { return 100; }
 
 uint64_t fk_kernel_launches(void) { return g_launches.load(); }
+
+int fk_debug_status(int reset, int *code, long long *index) {
+#ifdef FK_DEBUG
+    int (*readers[])(int, unsigned long long *) = {dbg_api, dbg_cc, dbg_tc, dbg_chi2, dbg_oz};
+    unsigned long long first = 0;
+    for (auto rd : readers) {
+        unsigned long long w = 0;
+        const int rc = rd(reset, &w);
+        if (rc) return rc;
+        if (!first) first = w;
+    }
+    if (code) *code = (int)(first >> 40);
+    if (index) *index = (long long)(first & ((1ull << 40) - 1));
+    return FK_OK;
+#else
+    (void)reset;
+    if (code) *code = 0;
+    if (index) *index = 0;
+    return fail(FK_EUNSUPPORTED, "fk_debug_status: not a debug build (libfk_debug.so)");
+#endif
+}
+
+int fk_debug_selftest(void) {
+#ifdef FK_DEBUG
+    int *buf = nullptr;
+    FK_CUDA(cudaMalloc(&buf, 4 * sizeof(int)));
+    unsigned long long w = 0;
+    int rc = dbg_api(1, &w);
+    if (!rc) {
+        k_dbg_selftest<<<1, 1>>>(buf, 4, 4);  // index 4 of 4: the check must catch it
+        count_launch();
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e) rc = cuda_fail(e, "fk_debug_selftest");
+    }
+    if (!rc) rc = dbg_api(1, &w);
+    cudaFree(buf);
+    if (rc) return rc;
+    if ((w >> 40) != 99 || (w & ((1ull << 40) - 1)) != 4)
+        return fail(FK_ECUDA, "fk_debug_selftest: the failed check was not reported");
+    return FK_OK;
+#else
+    return fail(FK_EUNSUPPORTED, "fk_debug_selftest: not a debug build (libfk_debug.so)");
+#endif
+}
 
 int fk_device_status(int reset) {
     const int a = device_status(reset);

@@ -30,19 +30,78 @@ int cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::fk::cuda_fail(e_, #call); \
     } while (0)
 
+// Debug builds (-DFK_DEBUG, libfk_debug.so): index checks in the kernels
+// raise a device word holding the first failed check's code and index, and
+// skip the access, instead of touching memory out of range; per-call scratch
+// buffers carry guard bytes that are checked when the call's scratch is
+// released.  Release builds compile every check away.  Each translation unit
+// has its own word (static), read by its dbg_* function.
+#ifdef FK_DEBUG
+static __device__ unsigned long long g_fk_dbg;
+__device__ __forceinline__ bool fk_dbg_ok(bool cond, int code, long long idx) {
+    if (!cond)
+        atomicCAS(&g_fk_dbg, 0ull,
+                  ((unsigned long long)code << 40) | ((unsigned long long)idx & ((1ull << 40) - 1)));
+    return cond;
+}
+#define FK_DBG(cond, code, idx) fk_dbg_ok((cond), (code), (long long)(idx))
+constexpr size_t FK_GUARD_BYTES = 256;
+constexpr unsigned char FK_GUARD_BYTE = 0xA5;
+static __global__ void k_guard_check(const unsigned char *g) {
+    for (unsigned i = threadIdx.x; i < FK_GUARD_BYTES; i += blockDim.x)
+        if (g[i] != FK_GUARD_BYTE) {
+            fk_dbg_ok(false, 90, i);
+            break;
+        }
+}
+#define FK_DBG_READER(fn)                                                                    \
+    int fn(int reset, unsigned long long *w) {                                               \
+        FK_CUDA(cudaMemcpyFromSymbol(w, g_fk_dbg, sizeof(*w)));                              \
+        if (reset) {                                                                         \
+            const unsigned long long z = 0;                                                  \
+            FK_CUDA(cudaMemcpyToSymbol(g_fk_dbg, &z, sizeof(z)));                            \
+        }                                                                                    \
+        return FK_OK;                                                                        \
+    }
+#else
+#define FK_DBG(cond, code, idx) true
+#define FK_DBG_READER(fn)                                                                    \
+    int fn(int, unsigned long long *w) {                                                     \
+        *w = 0;                                                                              \
+        return FK_OK;                                                                        \
+    }
+#endif
+
 // Stream-ordered scratch memory for one call (cudaMallocAsync/cudaFreeAsync).
 struct Scratch {
     cudaStream_t stream;
     std::vector<void *> ptrs;
+#ifdef FK_DEBUG
+    std::vector<unsigned char *> guards;
+#endif
     explicit Scratch(cudaStream_t s) : stream(s) {}
     ~Scratch() {
+#ifdef FK_DEBUG
+        for (unsigned char *g : guards) k_guard_check<<<1, 256, 0, stream>>>(g);
+#endif
         for (void *p : ptrs) cudaFreeAsync(p, stream);
     }
     template <typename T>
     cudaError_t get(T **p, size_t count) {
         void *q = nullptr;
+#ifdef FK_DEBUG
+        const size_t used = (count * sizeof(T) + 15) / 16 * 16;
+        cudaError_t e = cudaMallocAsync(&q, used + FK_GUARD_BYTES + 256, stream);
+        if (e == cudaSuccess) {
+            ptrs.push_back(q);
+            unsigned char *g = static_cast<unsigned char *>(q) + used;
+            guards.push_back(g);
+            e = cudaMemsetAsync(g, FK_GUARD_BYTE, FK_GUARD_BYTES, stream);
+        }
+#else
         cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 256, stream);
         if (e == cudaSuccess) ptrs.push_back(q);
+#endif
         *p = reinterpret_cast<T *>(q);
         return e;
     }
@@ -185,6 +244,13 @@ int cc_device_status(int reset);
 // zero-filled outside the array (k_tc.cu)
 int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_cols,
                    int box_rows);
+// debug-build check words of each translation unit (0 when clean or in a
+// release build): code << 40 | index of the first failed check
+int dbg_cc(int reset, unsigned long long *w);
+int dbg_tc(int reset, unsigned long long *w);
+int dbg_chi2(int reset, unsigned long long *w);
+int dbg_oz(int reset, unsigned long long *w);
+int dbg_api(int reset, unsigned long long *w);
 // conversion helpers (k_cc.cu)
 int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
                  float *d32, cudaStream_t s);

@@ -157,21 +157,52 @@ __global__ void __launch_bounds__(256) k_stream(TableView tv, const T *__restric
         for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         const int d = d0 + dd;
         if (lane == 0 && d < tv.ndata)
-            part[((size_t)blockIdx.x * R + r) * tv.ndata + d] = v;
+            if (FK_DBG(r < R && d < tv.ndata, 1, d)) part[((size_t)blockIdx.x * R + r) * tv.ndata + d] = v;
     }
 }
 
-// O[r][d] (+)= sum_k part[(k * R + r) * ndata + d], k ascending.
+// O[r][d] = sum_k part[(k * R + r) * ndata + d] in a fixed order: k
+// ascending when there are few parts; with WIDE_PARTS or more (long rows
+// streamed by many chunks, e.g. a dense table with K = 10^7) one warp per
+// output, lane l adding parts l, l + 32, ... and a butterfly sum of the lanes,
+// so that the loads of all parts are in flight together.  The order depends
+// only on nparts, a property of the table.
+constexpr int WIDE_PARTS = 64;
 template <typename T>
 __global__ void k_reduce_parts(const T *__restrict__ part, int nparts, int ndata, int R,
                                T *__restrict__ O, int ldo) {
+    const long long n = (long long)R * ndata;
+    if (nparts >= WIDE_PARTS) {
+        const long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int lane = threadIdx.x & 31;
+        if (idx >= n) return;  // whole warps leave together
+        const T *p = part + idx;
+        T s = T(0);
+        for (int k = lane; k < nparts; k += 32) s += p[(size_t)k * n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const long long r = idx / ndata, d = idx - r * ndata;
+        if (lane == 0 && FK_DBG(r < R && d < ndata && d < ldo, 2, idx)) O[r * ldo + d] = s;
+        return;
+    }
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)R * ndata) return;
+    if (idx >= n) return;
     const T *p = part + idx;
     T s = T(0);
-    for (int k = 0; k < nparts; ++k) s += p[(size_t)k * R * ndata];
+    for (int k = 0; k < nparts; ++k) s += p[(size_t)k * n];
     const long long r = idx / ndata, d = idx - r * ndata;
-    O[r * ldo + d] = s;
+    if (FK_DBG(r < R && d < ndata && d < ldo, 2, idx)) O[r * ldo + d] = s;
+}
+
+// launch of k_reduce_parts (one thread or one warp per output)
+template <typename T>
+int reduce_parts(const T *part, int nparts, int ndata, int R, T *O, int ldo, cudaStream_t s) {
+    const long long n = (long long)R * ndata;
+    const long long threads = nparts >= WIDE_PARTS ? n * 32 : n;
+    k_reduce_parts<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(part, nparts, ndata, R, O, ldo);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
 }
 
 // ----------------------------------------------------------------------------
@@ -694,7 +725,9 @@ __global__ void k_bwd_dis_gather(TableView tv, const T *__restrict__ P, int nspl
     T s = T(0);
     for (int z = 0; z < nsplit; ++z) s += P[((size_t)z * R + r) * tv.E + e];
     const int k = e / tv.nx, i = e - k * tv.nx;
-    gF[((size_t)r * NFL + tv.ca[k]) * tv.nxg + tv.xmap[i]] += s;
+    const int a = tv.ca[k], m = tv.xmap[i];
+    if (FK_DBG(a >= 0 && a < NFL && m >= 0 && m < tv.nxg && k < tv.nch, 3, e))
+        gF[((size_t)r * NFL + a) * tv.nxg + m] += s;
 }
 
 // FP64 rows (staging, [rows][E]) -> padded stream layouts.
@@ -805,11 +838,7 @@ int fwd_cc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *fk, c
         count_launch();
         FK_CUDA(cudaGetLastError());
     }
-    const long long n = (long long)R * t->ndata;
-    k_reduce_parts<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nparts, t->ndata, R, O, ldo);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    return FK_OK;
+    return reduce_parts<T>(part, nparts, t->ndata, R, O, ldo, s);
 }
 
 template <typename T>
@@ -896,6 +925,7 @@ __global__ void __launch_bounds__(256) k_lum(TableView tv, const T *__restrict__
         const int e = (int)(idx - r * tv.E);
         const int c = e / nx2, rem = e - c * nx2, i = rem / tv.nx, j = rem - i * tv.nx;
         const T *f = F + (size_t)r * NFL * tv.nxg;
+        if (!FK_DBG(c < tv.nch, 4, idx)) continue;
         L[idx] = __ldg(f + __ldg(tv.ca + c) * tv.nxg + __ldg(tv.xmap + i)) *
                  __ldg(f + __ldg(tv.cb + c) * tv.nxg + __ldg(tv.xmap + j));
     }
@@ -928,6 +958,8 @@ int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, vo
     return bwd_cc_t<float>(t, (const float *)F, (const float *)gO, ldgo, R, (float *)gF,
                            accumulate, t->fk32, s);
 }
+
+FK_DBG_READER(dbg_cc)
 
 int convert_rows(const double *d_src, long long rows, long long E, long long ldE, double *d64,
                  float *d32, cudaStream_t s) {
@@ -1035,11 +1067,7 @@ int had_noalloc_t(const fk_table *t, const T *F, int R, T *O, int ldo, const T *
         rc = launch_fac<T>(t, F, R, fk, nparts, part, s);
         if (rc) return rc;
     }
-    const long long n = (long long)R * t->ndata;
-    k_reduce_parts<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nparts, t->ndata, R, O, ldo);
-    count_launch();
-    FK_CUDA(cudaGetLastError());
-    return FK_OK;
+    return reduce_parts<T>(part, nparts, t->ndata, R, O, ldo, s);
 }
 
 }  // namespace

@@ -168,7 +168,10 @@ __device__ void blocked_solve(const double *__restrict__ P, long long sm, long l
                               const double *__restrict__ Dinv, int n, double *v,
                               double (*part)[RT][PB], double *Ds) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    auto at = [&](int rr, int i) -> double & { return v[rr * n + (REV ? n - 1 - i : i)]; };
+    auto at = [&](int rr, int i) -> double & {
+        const int j = REV ? n - 1 - i : i;
+        return v[FK_DBG(j >= 0 && j < n && rr < RT, 20, j) ? rr * n + j : 0];
+    };
     for (int i0 = 0; i0 < n; i0 += PB) {
         const int rows = min(PB, n - i0);
         const bool own = lane < rows;  // lane owns row i0 + lane
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_chi2_solve(CovView cv, const 
     blocked_solve<RT, true>(Lk + (long long)(n - 1) * (n + 1), -(long long)n, -1, cv.DU + cv.doff[k], n, v, part, Ds);
     for (int idx = threadIdx.x; idx < RT * n; idx += SOLVE_THREADS) {
         const int rr = idx / n, i = idx - rr * n, r = r0 + rr;
-        if (r < R) gO[(size_t)r * cv.n + off + i] = (TO)(2.0 * v[idx]);
+        if (r < R && FK_DBG(off + i < cv.n, 21, off + i)) gO[(size_t)r * cv.n + off + i] = (TO)(2.0 * v[idx]);
     }
 }
 
@@ -267,6 +270,12 @@ __global__ void k_chi2_sum(const double *__restrict__ zsq, int nblocks, int R, d
     for (int k = 0; k < nblocks; ++k) s += zsq[(size_t)k * R + r];
     chi2[r] = s;
 }
+
+}  // namespace
+
+FK_DBG_READER(dbg_chi2)
+
+namespace {
 
 CovView cview(const fk_cov *c) {
     return CovView{c->n, c->d_sizes, c->d_offs, c->d_loff, c->d_doff, c->L, c->LT, c->DL, c->DU};

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *__restrict__ src
         if (kk < kn && row < nrows) {
             const long long k = k0 + kk;
             long long col = kmeta ? (long long)__ldg(kmeta + k) : (k < K ? k : -1);
-            if (col >= 0) v[j] = trans ? src[col * ld + row] : src[(long long)row * ld + col];
+            if (col >= 0 && FK_DBG(trans ? row < ld : col < ld, 30, col))
+                v[j] = trans ? src[col * ld + row] : src[(long long)row * ld + col];
         }
         mx = max(mx, abs_bits(v[j]));
     }
@@ -121,7 +122,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double *__restrict__ src
             const int sh = OZ_B * (OZ_S - 1 - p);
             const long long t = sh ? (N + (1LL << (sh - 1))) >> sh : N;
             N -= t * (1LL << sh);
-            out[((size_t)p * rows_pad + row) * ktot_pad + k0 + kk] = __float2bfloat16_rn((float)t);
+            if (FK_DBG(row < rows_pad && k0 + kk < ktot_pad && t >= -64 && t <= 64, 31, t))
+                out[((size_t)p * rows_pad + row) * ktot_pad + k0 + kk] = __float2bfloat16_rn((float)t);
         }
     }
 }
@@ -168,7 +170,8 @@ __global__ void k_oz_dis_scatter(const double *__restrict__ W, int R, int E, int
     if (idx >= (long long)R * E) return;
     const int r = (int)(idx / E), e = (int)(idx - (long long)r * E);
     const int k = e / nx, i = e - k * nx;
-    gF[((size_t)r * NFL + __ldg(ca + k)) * nxg + __ldg(xmap + i)] += W[idx];
+    const int a = __ldg(ca + k), m = __ldg(xmap + i);
+    if (FK_DBG(a >= 0 && a < NFL && m >= 0 && m < nxg, 32, e)) gF[((size_t)r * NFL + a) * nxg + m] += W[idx];
 }
 
 // Hadronic adjoint from W[r][(c, i, j)] = sum_d gO[r][d] FK[d][c][i][j]:
@@ -285,6 +288,8 @@ int oz_run(const fk_table *t, const TcPack &pk, const int *pe, int kchunk, const
 }
 
 }  // namespace
+
+FK_DBG_READER(dbg_oz)
 
 int oz_build(fk_table *t, const double *host_fk) {
     TcLayout &L = t->tc;

@@ -745,9 +745,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (MODE == MODE_ADJ) {
                     float *pg = p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r;
+                    if (FK_DBG(nt < p.ntile_n && r < p.R_pad, 14, nt)) {
 #pragma unroll
-                    for (int i = 0; i < MI; ++i)
-                        if (i < p.nx) pg[(size_t)i * p.R_pad] = ps[i];
+                        for (int i = 0; i < MI; ++i)
+                            if (i < p.nx) pg[(size_t)i * p.R_pad] = ps[i];
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -850,8 +852,9 @@ __global__ void __launch_bounds__(256) k_pack_pdf(const int *__restrict__ kmeta,
         const float *Fr = F + (size_t)r * frow;
         float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (r < R && o[u] >= 0) ? __ldg(Fr + o[u]) : 0.f;
-        store8<PREC>((size_t)r * ktot_pad + k0, v, hi, lo, f32);
+        for (int u = 0; u < 8; ++u)
+            v[u] = (r < R && o[u] >= 0 && FK_DBG(o[u] < frow, 10, o[u])) ? __ldg(Fr + o[u]) : 0.f;
+        if (FK_DBG(r < R_pad && k0 + 8 <= ktot_pad, 11, k0)) store8<PREC>((size_t)r * ktot_pad + k0, v, hi, lo, f32);
     }
 }
 
@@ -950,7 +953,7 @@ __global__ void __launch_bounds__(128) k_adj_gather(const float *__restrict__ P1
         }
     }
     const size_t o = ((size_t)r * NFL + a) * nxg + m;
-    gF[o] = accumulate ? gF[o] + s : s;
+    if (FK_DBG(i < nx, 12, i)) gF[o] = accumulate ? gF[o] + s : s;
 }
 
 // ------------------------------------------------------------ host ----
@@ -1601,7 +1604,8 @@ __global__ void k_dis_scatter(const float *__restrict__ P, int R, int E, int nx,
     if (idx >= (long long)R * E) return;
     const int r = (int)(idx / E), e = (int)(idx - (long long)r * E);
     const int k = e / nx, i = e - k * nx;
-    gF[((size_t)r * NFL + __ldg(ca + k)) * nxg + __ldg(xmap + i)] += P[idx];
+    const int a = __ldg(ca + k), m = __ldg(xmap + i);
+    if (FK_DBG(a >= 0 && a < NFL && m >= 0 && m < nxg, 13, e)) gF[((size_t)r * NFL + a) * nxg + m] += P[idx];
 }
 
 template <int PREC>
@@ -1736,6 +1740,8 @@ int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, lon
     if (r != CUDA_SUCCESS) return fail(FK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return FK_OK;
 }
+
+FK_DBG_READER(dbg_tc)
 
 int device_status(int reset) {
     int v = 0;

@@ -15,11 +15,22 @@
 //    compute every replica row independently of the others;
 //  - each batch runs on its own stream: pinned H2D of the PDFs, the
 //    convolution, D2H of each request's observables, then a host callback
-//    marks the requests done and returns their bytes to the budget.
+//    marks the requests done and returns their bytes to the budget;
+//  - failure detection: every failure ends in a per-ticket status.  A batch
+//    whose completion callback has not arrived once its stream has finished
+//    and a grace period has passed (a lost completion message) has its
+//    requests failed with FK_ETIMEDOUT and its budget returned; a request can
+//    be cancelled (FK_ECANCELED); destroying a server fails what never
+//    started and waits for what is running.  Host-side faults (a failed
+//    pinned or device allocation, a failed launch, a dropped completion) can
+//    be injected with fk_serve_inject or the FK_FAULT environment variable,
+//    to test these paths without any fault on the GPU.
 #include "fk_internal.h"
 
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
+#include <string>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -39,6 +50,13 @@ struct Batch {
     std::vector<Request *> reqs;
     size_t bytes = 0;
     int stream = 0;
+    std::chrono::steady_clock::time_point t0;  // when its work was enqueued
+};
+
+// a batch whose completion message was lost, with an event after its work
+struct Unconfirmed {
+    Batch *b;
+    cudaEvent_t ev;
 };
 
 struct Request {
@@ -49,6 +67,7 @@ struct Request {
     void *O = nullptr;  // pinned
     int status = FK_OK;
     bool done = false;
+    bool cancelled = false;
 };
 
 // Pinned host buffers for request staging.  Pinning is slow (milliseconds per
@@ -152,10 +171,55 @@ struct fk_server {
 
     uint64_t completed = 0, dp_rep = 0, launches = 0;
     size_t peak_bytes = 0;
+
+    // failure detection and injection
+    int faults[FK_FAULT_DROP + 1] = {};   // armed host-side faults, by kind
+    std::vector<Unconfirmed> unconfirmed; // batches whose completion message was lost
+    int grace_ms = 200;                   // after the stream is idle, before a batch is given up
+    uint64_t timed_out = 0;
 };
 
 namespace fk {
 namespace {
+
+// Takes one armed fault of this kind (caller holds s->mu or none is needed).
+bool take_fault(fk_server *s, int kind) {
+    std::lock_guard<std::mutex> l(s->mu);
+    if (s->faults[kind] <= 0) return false;
+    --s->faults[kind];
+    return true;
+}
+
+// Batches whose completion message never came: once the work they enqueued
+// has finished (their event) and the grace period has passed, their requests
+// fail with FK_ETIMEDOUT and their budget is returned.  Caller holds s->mu.
+bool reap_unconfirmed(fk_server *s) {
+    auto &v = s->unconfirmed;
+    bool any = false;
+    const auto now = std::chrono::steady_clock::now();
+    for (size_t i = 0; i < v.size();) {
+        Batch *b = v[i].b;
+        const bool finished = cudaEventQuery(v[i].ev) == cudaSuccess;
+        if (finished && now - b->t0 > std::chrono::milliseconds(s->grace_ms)) {
+            for (Request *r : b->reqs) {
+                r->status = FK_ETIMEDOUT;
+                r->done = true;
+            }
+            s->inflight--;
+            s->inflight_bytes -= b->bytes;
+            s->timed_out += b->reqs.size();
+            cudaEventDestroy(v[i].ev);
+            delete b;
+            v.erase(v.begin() + i);
+            any = true;
+        } else {
+            ++i;
+        }
+    }
+    return any;
+}
+
+bool has_unconfirmed(const fk_server *s) { return !s->unconfirmed.empty(); }
 
 void CUDART_CB batch_done(void *arg) {
     Batch *b = static_cast<Batch *>(arg);
@@ -186,7 +250,7 @@ void launch_batch(fk_server *s, Batch *b) {
     char *dF = nullptr, *dO = nullptr;
     int rc = FK_OK;
     const size_t fb = esz * (size_t)R * NFL * t->nxg, ob = esz * (size_t)R * t->ndata;
-    cudaError_t e = cudaMallocAsync((void **)&dF, fb, st);
+    cudaError_t e = take_fault(s, FK_FAULT_DEVICE) ? cudaErrorMemoryAllocation : cudaMallocAsync((void **)&dF, fb, st);
     if (!e) e = cudaMallocAsync((void **)&dO, ob, st);
     if (e) rc = cuda_fail(e, "serve: device buffers");
     size_t off = 0;
@@ -196,6 +260,7 @@ void launch_batch(fk_server *s, Batch *b) {
         if (e) rc = cuda_fail(e, "serve: H2D");
         off += r->f_bytes;
     }
+    if (!rc && take_fault(s, FK_FAULT_LAUNCH)) rc = fail(FK_ECUDA, "serve: convolution launch failed (injected)");
     if (!rc) {
         rc = t->kind == FK_KIND_HAD ? fk_had_conv(t, dF, R, dO, 0, prec, st)
                                     : fk_dis_conv(t, dF, R, dO, 0, prec, st);
@@ -209,6 +274,21 @@ void launch_batch(fk_server *s, Batch *b) {
     }
     if (dF) cudaFreeAsync(dF, st);
     if (dO) cudaFreeAsync(dO, st);
+    b->t0 = std::chrono::steady_clock::now();
+    if (!rc && take_fault(s, FK_FAULT_DROP)) {
+        // the completion message is lost: only the watchdog can finish this batch
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (!e) e = cudaEventRecord(ev, st);
+        if (e) {
+            rc = cuda_fail(e, "serve: completion event");
+        } else {
+            std::lock_guard<std::mutex> l(s->mu);
+            s->unconfirmed.push_back({b, ev});
+            s->cv_sched.notify_all();  // the scheduler starts polling for it
+            return;
+        }
+    }
     if (!rc) {
         e = cudaLaunchHostFunc(st, batch_done, b);
         if (e) rc = cuda_fail(e, "serve: completion callback");
@@ -246,13 +326,21 @@ int kernel_class(const fk_table *t, int prec, int R) {
 void scheduler(fk_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> l(s->mu);
+    auto ready = [&] { return s->stop || (!s->queue.empty() && s->inflight < s->max_inflight); };
     while (true) {
-        s->cv_sched.wait(l, [&] { return s->stop || (!s->queue.empty() && s->inflight < s->max_inflight); });
+        while (!ready()) {
+            if (has_unconfirmed(s)) {  // poll the lost completions every 10 ms
+                s->cv_sched.wait_for(l, std::chrono::milliseconds(10));
+                if (reap_unconfirmed(s)) s->cv_done.notify_all();
+            } else {
+                s->cv_sched.wait(l);
+            }
+        }
         if (s->stop && s->queue.empty()) break;
         if (s->stop) {
-            // drop what never started
+            // what never started is cancelled
             for (Request *r : s->queue) {
-                r->status = FK_ECUDA;
+                r->status = FK_ECANCELED;
                 r->done = true;
             }
             s->queue.clear();
@@ -270,7 +358,8 @@ void scheduler(fk_server *s) {
                 s->queue.pop_front();
                 s->cv_done.notify_all();
             } else {
-                s->cv_sched.wait(l);
+                s->cv_sched.wait_for(l, std::chrono::milliseconds(10));
+                if (reap_unconfirmed(s)) s->cv_done.notify_all();
             }
             continue;
         }
@@ -303,8 +392,11 @@ void scheduler(fk_server *s) {
         launch_batch(s, b);
         l.lock();
     }
-    // wait for the batches in flight
-    s->cv_done.wait(l, [&] { return s->inflight == 0; });
+    // wait for the batches in flight (and give up the lost ones)
+    while (s->inflight > 0) {
+        s->cv_done.wait_for(l, std::chrono::milliseconds(10));
+        if (reap_unconfirmed(s)) s->cv_done.notify_all();
+    }
 }
 
 }  // namespace
@@ -329,6 +421,24 @@ int fk_serve_create(size_t hbm_budget_bytes, int max_inflight, fk_server **out) 
             return fail(FK_ECUDA, "fk_serve_create: stream");
         }
         s->streams.push_back(st);
+    }
+    // FK_FAULT="kind:count,...": host-side faults armed at creation (kinds
+    // pinned, device, launch, drop), as fk_serve_inject
+    if (const char *env = std::getenv("FK_FAULT")) {
+        std::string spec(env);
+        size_t pos = 0;
+        while (pos < spec.size()) {
+            size_t end = spec.find(',', pos);
+            if (end == std::string::npos) end = spec.size();
+            const std::string item = spec.substr(pos, end - pos);
+            const size_t colon = item.find(':');
+            const std::string kind = item.substr(0, colon);
+            const int count = colon == std::string::npos ? 1 : std::atoi(item.c_str() + colon + 1);
+            const int k = kind == "pinned" ? FK_FAULT_PINNED : kind == "device" ? FK_FAULT_DEVICE
+                          : kind == "launch" ? FK_FAULT_LAUNCH : kind == "drop" ? FK_FAULT_DROP : 0;
+            if (k && count > 0) s->faults[k] += count;
+            pos = end + 1;
+        }
     }
     s->worker = std::thread(scheduler, s);
     *out = s;
@@ -370,9 +480,10 @@ int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int p
         if (s->resident + r->dev_bytes > s->budget)
             return fail(FK_EBUDGET, "request can never fit the server budget");
     }
-    size_t c1, c2;
-    r->F = s->pinned.get(r->f_bytes, &c1);
-    r->O = s->pinned.get(r->o_bytes, &c2);
+    size_t c1 = 0, c2 = 0;
+    const bool injected = take_fault(s, FK_FAULT_PINNED);
+    r->F = injected ? nullptr : s->pinned.get(r->f_bytes, &c1);
+    r->O = injected ? nullptr : s->pinned.get(r->o_bytes, &c2);
     if (!r->F || !r->O) {
         s->pinned.put(r->F, c1);
         s->pinned.put(r->O, c2);
@@ -393,7 +504,7 @@ int fk_serve_submit(fk_server *s, int table_id, const void *F_host, int R, int p
 static int finish(fk_server *s, std::unique_lock<std::mutex> &l, uint64_t ticket, void *O_host) {
     auto it = s->reqs.find(ticket);
     Request *r = it->second.get();
-    const int st = r->status;
+    const int st = r->cancelled && r->status == FK_OK ? FK_ECANCELED : r->status;
     if (st == FK_OK && O_host) std::memcpy(O_host, r->O, r->o_bytes);
     s->pinned.put(r->F, pow2_class(r->f_bytes));
     s->pinned.put(r->O, pow2_class(r->o_bytes));
@@ -422,8 +533,35 @@ int fk_serve_wait(fk_server *s, uint64_t ticket, void *O_host, int timeout_ms) {
     Request *r = it->second.get();
     const bool ok = s->cv_done.wait_for(l, std::chrono::milliseconds(std::max(0, timeout_ms)),
                                         [&] { return r->done; });
-    if (!ok) return fail(FK_ETIMEDOUT, "request still running");
+    if (!ok) return fail(FK_EPENDING, "request still running after the wait");
     return finish(s, l, ticket, O_host);
+}
+
+int fk_serve_cancel(fk_server *s, uint64_t ticket) {
+    if (!s) return fail(FK_EINVAL, "fk_serve_cancel: null server");
+    std::lock_guard<std::mutex> l(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(FK_ENOTFOUND, "unknown ticket");
+    Request *r = it->second.get();
+    if (r->done) return FK_OK;  // finished already: its result stands
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q != s->queue.end()) {  // not started: it never will
+        s->queue.erase(q);
+        r->status = FK_ECANCELED;
+        r->done = true;
+        s->cv_done.notify_all();
+    } else {
+        r->cancelled = true;  // running: its result will be discarded
+    }
+    return FK_OK;
+}
+
+int fk_serve_inject(fk_server *s, int fault, int count) {
+    if (!s || fault < FK_FAULT_PINNED || fault > FK_FAULT_DROP || count < 0)
+        return fail(FK_EINVAL, "fk_serve_inject: bad server, fault kind or count");
+    std::lock_guard<std::mutex> l(s->mu);
+    s->faults[fault] = count;
+    return FK_OK;
 }
 
 int fk_serve_stats(const fk_server *cs, uint64_t *completed, uint64_t *dp_rep, uint64_t *launches,

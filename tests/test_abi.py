@@ -91,3 +91,19 @@ def test_dense_table_k_limit_needs_no_gpu():
     # the limit is checked before the table is read
     assert lib.fk_table_create_dense(buf.ctypes.data_as(ctypes.c_void_p), 1, (1 << 30) + 1,
                                      1 << _lib.FK_FP32, ctypes.byref(out)) == _lib.FK_EINVAL
+
+
+def test_debug_build_exports_and_release_reports_no_debug():
+    """libfk_debug.so (FK_DEBUG defined) exports the same boundary; the
+    release library answers the debug queries with FK_EUNSUPPORTED, without
+    touching a GPU."""
+    from paper_1909_10547_b300 import build as _b
+    path = _b.build(debug=True)
+    dbg = ctypes.CDLL(path)
+    missing = [n for n in sorted(declared()) if not hasattr(dbg, n)]
+    assert not missing, missing
+    lib = _lib.load()
+    code, idx = ctypes.c_int(-1), ctypes.c_longlong(-1)
+    assert lib.fk_debug_status(0, ctypes.byref(code), ctypes.byref(idx)) == _lib.FK_EUNSUPPORTED
+    assert code.value == 0 and idx.value == 0
+    assert lib.fk_debug_selftest() == _lib.FK_EUNSUPPORTED

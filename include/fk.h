@@ -89,6 +89,25 @@ enum {
     FK_FP64_TC = 5
 };
 #define FK_PREC_BIT(p) (1u << (p))
+/* Forward formulation of a hadronic table in the reduced modes (BF16,
+ * BF16X3, TF32), fixed when the table is created so that a replica's result
+ * never depends on R:
+ *  - factorised: the tensor cores contract (channel, x_j) for each first
+ *    flavour a and the epilogue applies f_a(x_i) and sums over x_i;
+ *  - dense: the paper's formulation (Sec. 3, Table 3), the table flattened
+ *    to [ndata][(c, i, j)] times the PDF matrix
+ *    L[r][(c, i, j)] = f_{a_c}(x_i) f_{b_c}(x_j), with L formed stage by stage
+ *    in shared memory (never in device memory) and K split into fixed runs
+ *    of 1536 columns whose partial results are added in a fixed order.  The
+ *    table then also stores the flattened packing.
+ * The factorised form is the default; FK_TABLE_LUMI in the prec_mask of
+ * fk_table_create_had selects the dense form (forming the PDF matrix costs
+ * the SM more issue slots per stage than the MMAs take, so it is slower on
+ * the tables measured), FK_TABLE_FACTORED states the default explicitly;
+ * fk_table_info reports FK_TABLE_LUMI in the mask when the dense form is
+ * used.  The adjoint is factorised in either case. */
+#define FK_TABLE_FACTORED (1u << 16)
+#define FK_TABLE_LUMI (1u << 17)
 /* Modes whose buffers are double: FK_FP64 and FK_FP64_TC. */
 #define FK_IO64(p) ((p) == FK_FP64 || (p) == FK_FP64_TC)
 
@@ -156,8 +175,9 @@ int fk_table_create_dis(const double *fk, int ndata, const int *flav, int nflav,
  * Hadronic FK table (Eq. 1): fk is HOST memory, [ndata][nc][nx][nx] FP64, one
  * nx*nx block per active channel c coupling flavour ca[c] at x_i (first x
  * index) with flavour cb[c] at x_j (second x index).  Channels are ordered
- * pairs and must be distinct; (a, a) is allowed.  Other arguments as for
- * fk_table_create_dis.
+ * pairs and must be distinct; (a, a) is allowed.  prec_mask may also hold
+ * one of FK_TABLE_FACTORED / FK_TABLE_LUMI (both: FK_EINVAL).  Other
+ * arguments as for fk_table_create_dis.
  */
 int fk_table_create_had(const double *fk, int ndata, const int *ca, const int *cb, int nc,
                         int nx, const int *xmap, int nx_grid, unsigned prec_mask,
@@ -166,7 +186,9 @@ int fk_table_create_had(const double *fk, int ndata, const int *ca, const int *c
 /* Frees the table's device memory.  NULL is accepted. */
 int fk_table_destroy(fk_table *t);
 
-/* Shape and resident size of a table.  Any output pointer may be NULL. */
+/* Shape and resident size of a table.  Any output pointer may be NULL.
+ * prec_mask holds the stored precisions, plus FK_TABLE_LUMI when the
+ * reduced-mode forward of a hadronic table uses the dense form. */
 int fk_table_info(const fk_table *t, int *kind, int *ndata, int *nchannels, int *nx,
                   int *nx_grid, unsigned *prec_mask, size_t *device_bytes);
 

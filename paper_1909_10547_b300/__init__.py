@@ -83,8 +83,10 @@ class Table:
         return cls(h, 0, nd, nfl, nx, nxg)
 
     @classmethod
-    def had(cls, fk, ca, cb, xmap=None, nx_grid=None, precs=("fp64", "fp32")):
-        """fk [ndata][nc][nx][nx] (host, FP64); channel c = (ca[c], cb[c])."""
+    def had(cls, fk, ca, cb, xmap=None, nx_grid=None, precs=("fp64", "fp32"), form=None):
+        """fk [ndata][nc][nx][nx] (host, FP64); channel c = (ca[c], cb[c]).
+        form: None (the library's choice), "factored" or "lumi" (the
+        reduced-mode forward's formulation, FK_TABLE_FACTORED / FK_TABLE_LUMI)."""
         fk = np.ascontiguousarray(fk, dtype=np.float64)
         nd, nc, nx, _ = fk.shape
         ca = np.ascontiguousarray(ca, dtype=np.int32)
@@ -92,8 +94,9 @@ class Table:
         xm = None if xmap is None else np.ascontiguousarray(xmap, dtype=np.int32)
         nxg = nx if nx_grid is None else int(nx_grid)
         h = ctypes.c_void_p()
+        mask = _mask(precs) | {None: 0, "factored": _lib.FK_TABLE_FACTORED, "lumi": _lib.FK_TABLE_LUMI}[form]
         _lib.call("fk_table_create_had", _p(fk), nd, _p(ca), _p(cb), nc, nx, _p(xm), nxg,
-                  _mask(precs), ctypes.byref(h))
+                  mask, ctypes.byref(h))
         return cls(h, 1, nd, nc, nx, nxg)
 
     @classmethod
@@ -109,16 +112,27 @@ class Table:
         return t
 
     @classmethod
-    def from_workload(cls, t, precs=("fp64", "fp32")):
-        """Builds a device table from a workloads.DisTable / HadTable."""
+    def from_workload(cls, t, precs=("fp64", "fp32"), form=None):
+        """Builds a device table from a workloads.DisTable / HadTable (form:
+        see had(); hadronic tables only)."""
         if hasattr(t, "ca"):
-            return cls.had(t.fk, t.ca, t.cb, t.xmap, t.nxg, precs)
+            return cls.had(t.fk, t.ca, t.cb, t.xmap, t.nxg, precs, form)
+        if form is not None:
+            raise ValueError("form applies to hadronic tables")
         return cls.dis(t.compact(), t.flav, t.xmap, t.nxg, precs)
 
     def device_bytes(self) -> int:
         n = ctypes.c_size_t()
         _lib.call("fk_table_info", self._h, None, None, None, None, None, None, ctypes.byref(n))
         return n.value
+
+    @property
+    def lumi(self) -> bool:
+        """True when the reduced-mode forward uses the dense formulation with
+        the PDF matrix formed in shared memory (FK_TABLE_LUMI)."""
+        m = ctypes.c_uint()
+        _lib.call("fk_table_info", self._h, None, None, None, None, None, ctypes.byref(m), None)
+        return bool(m.value & _lib.FK_TABLE_LUMI)
 
     @property
     def handle(self):

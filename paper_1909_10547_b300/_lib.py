@@ -118,6 +118,8 @@ def call(name, *args):
 FK_OK, FK_EINVAL, FK_ENOMEM, FK_EBUDGET, FK_EPENDING, FK_ETIMEDOUT, FK_ECUDA, FK_ENOTFOUND, \
     FK_EUNSUPPORTED, FK_ECANCELED = range(10)
 FK_FAULT_PINNED, FK_FAULT_DEVICE, FK_FAULT_LAUNCH, FK_FAULT_DROP = range(1, 5)
+# forward-formulation flags of fk_table_create_had (include/fk.h)
+FK_TABLE_FACTORED, FK_TABLE_LUMI = 1 << 16, 1 << 17
 FK_FP64, FK_FP32, FK_BF16, FK_BF16X3, FK_TF32, FK_FP64_TC = range(6)
 PRECS = {"fp64": FK_FP64, "fp32": FK_FP32, "bf16": FK_BF16, "bf16x3": FK_BF16X3, "tf32": FK_TF32,
          "fp64tc": FK_FP64_TC}

@@ -118,6 +118,11 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
     if (ndata < 1) return fail(FK_EINVAL, "ndata < 1");
     if (nx < 1 || nx > MAX_NX) return fail(FK_EINVAL, "nx must be in 1..64");
     if (nxg < nx || nxg > MAX_NXG) return fail(FK_EINVAL, "nx_grid must be in nx..64");
+    // the forward-formulation flags apply to hadronic tables only, one at a time
+    const unsigned form = mask & (FK_TABLE_FACTORED | FK_TABLE_LUMI);
+    mask &= ~(FK_TABLE_FACTORED | FK_TABLE_LUMI);
+    if (form && (kind != FK_KIND_HAD || form == (FK_TABLE_FACTORED | FK_TABLE_LUMI)))
+        return fail(FK_EINVAL, "FK_TABLE_FACTORED / FK_TABLE_LUMI: one of them, hadronic tables only");
     if (!mask || (mask & ~ALL_PRECS)) return fail(FK_EINVAL, "bad precision mask");
     const int maxch = kind == FK_KIND_HAD ? MAX_CH : NFL;
     if (nch < 1 || nch > maxch) return fail(FK_EINVAL, "channel count out of range");
@@ -160,7 +165,7 @@ int table_create(int kind, const double *fk, int ndata, const int *ca, const int
         return rc;
     }
     if (mask & TC_PRECS) {
-        rc = kind == FK_KIND_HAD ? tc_build(t, fk) : tc_build_dis(t, fk);
+        rc = kind == FK_KIND_HAD ? tc_build(t, fk, form) : tc_build_dis(t, fk);
         if (rc) {
             table_free(t);
             return rc;
@@ -328,7 +333,7 @@ int fk_table_info(const fk_table *t, int *kind, int *ndata, int *nchannels, int 
     if (nchannels) *nchannels = t->nch;
     if (nx) *nx = t->nx;
     if (nx_grid) *nx_grid = t->nxg;
-    if (prec_mask) *prec_mask = t->mask;
+    if (prec_mask) *prec_mask = t->mask | (t->tc.lum_on ? FK_TABLE_LUMI : 0u);
     if (device_bytes) *device_bytes = t->bytes;
     return FK_OK;
 }

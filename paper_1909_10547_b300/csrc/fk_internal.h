@@ -164,6 +164,15 @@ struct TcLayout {
     TcPack oz, ozT;
     int *oz_e = nullptr, *ozT_e = nullptr;
     int oz_kchunk = 0, ozT_kchunk = 0;
+    // The paper's dense formulation of the hadronic forward (Sec. 3, Table
+    // 3) with the PDF matrix formed in shared memory: the table flattened to
+    // [ndata][(c, i, j)], j padded to lum_nxp (a power of two, 16 to 64,
+    // zeros past nx); lum_mmeta[a * nx + x] = a * nx_grid + xmap[x], the F offsets of
+    // the builders' transposed PDF rows.  lum_on: the forward uses it.
+    TcPack lum;
+    int lum_nxp = 0;
+    int *lum_mmeta = nullptr;
+    bool lum_on = false;
 };
 
 }  // namespace fk
@@ -210,7 +219,8 @@ int luminosity_cc(const fk_table *t, const void *F, int R, void *L, bool f64, cu
 int bwd_cc(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,
            int accumulate, bool f64, cudaStream_t s);
 // tensor-core path (k_tc.cu)
-int tc_build(fk_table *t, const double *host_fk);
+// form: 0 (automatic), FK_TABLE_FACTORED or FK_TABLE_LUMI
+int tc_build(fk_table *t, const double *host_fk, unsigned form);
 int fwd_tc(const fk_table *t, const float *F, int R, float *O, int ldo, int prec, cudaStream_t s);
 int tc_build_dense(fk_table *t, const double *host_fk);
 int dense_tc(const fk_table *t, const float *L, int R, float *O, int ldo, int prec, cudaStream_t s);

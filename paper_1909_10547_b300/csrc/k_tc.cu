@@ -276,6 +276,13 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
         : "memory");
 }
 
+// TF32 operand value: FP32 rounded to the nearest TF32, ties away from zero
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
 // ------------------------------------------------------------ kernel ----
 template <int PREC>
 struct Tr {
@@ -296,6 +303,27 @@ template <int PREC, int CL>
 __host__ __device__ constexpr int tc_stages() {
     return CL == 2 ? 3 : 2;
 }
+
+// Epilogue modes of the tensor-core kernel.
+//  FWD: O[r][d]   = sum_g sum_i f^r_{a_g}(x_i) Y_g[r][(i, d)]
+//  ADJ: P[t][g][i][r] = sum_{d in tile t} gO[r][d] Y_g[r][(i, d)]
+// (with the transposed packing, i stands for x_j and g for the second flavour)
+// MODE_DENSE: the plain product of the paper's Table 3 (one group spanning K,
+// the accumulator columns are the tile's data points, stored as they are)
+// MODE_LUMI: the same product for a hadronic table flattened to
+// [ndata][(c, i, j)], with the A operand, the PDF matrix
+// L[r][(c, i, j)] = f^r_{a_c}(x_i) f^r_{b_c}(x_j), formed stage by stage in
+// shared memory by eight builder warps instead of loaded
+enum { MODE_FWD = 0, MODE_ADJ = 1, MODE_DENSE = 2, MODE_LUMI = 3 };
+// builder warps of MODE_LUMI (two per A row: each forms half of a stage's columns)
+constexpr int LB_WARPS = 8;
+template <int MODE>
+__host__ __device__ constexpr int tc_threads() {
+    return MODE == MODE_LUMI ? TC_THREADS + 32 * LB_WARPS : TC_THREADS;
+}
+// K columns per split of a MODE_LUMI product: a table property, so a
+// replica's result does not depend on R
+constexpr int LUMI_KSPLIT = 1536;
 
 struct TcParams {
     int ntiles, nrt, nchunks, n_rows, ngroups, nx, ndata, R, R_pad, ldo;
@@ -323,15 +351,16 @@ struct TcParams {
     // its stages run pair j = q / spc over the split's K (stage q % spc), and
     // pair u of the launch stands for pairs pa/pb[u * npc + j]
     int npc, spc;
+    // MODE_LUMI: FT[(a * nx + x) * R_pad + r] = f^r_a(x_x) for the builders;
+    // lfl[c] = a_c, lfl[MAX_CH + c] = b_c, the flavours of the table's lnc
+    // channels (in the parameters: the builders' addresses need no load from
+    // memory); K columns are (c, i, j) with j padded to lnxp (a power of two,
+    // 16 to 64) and read as zero from j = nx
+    const float *FT;
+    uint8_t lfl[2 * MAX_CH];
+    int lnc, lnxp;
 };
 
-// Epilogue modes of the tensor-core kernel.
-//  FWD: O[r][d]   = sum_g sum_i f^r_{a_g}(x_i) Y_g[r][(i, d)]
-//  ADJ: P[t][g][i][r] = sum_{d in tile t} gO[r][d] Y_g[r][(i, d)]
-// (with the transposed packing, i stands for x_j and g for the second flavour)
-// MODE_DENSE: the plain product of the paper's Table 3 (one group spanning K,
-// the accumulator columns are the tile's data points, stored as they are)
-enum { MODE_FWD = 0, MODE_ADJ = 1, MODE_DENSE = 2 };
 
 template <int PREC, int CL>
 size_t tc_smem_bytes(int n_rows) {
@@ -349,7 +378,7 @@ size_t tc_smem_bytes(int n_rows) {
 //  complete on its `full` barriers, its commits release `empty` and signal
 //  `accf` in both CTAs, and both CTAs' epilogues release its `acce`.
 template <int PREC, int G, int MODE, int CL>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(tc_threads<MODE>(), 1)
     k_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
          const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
          TcParams p) {
@@ -406,7 +435,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool dead = false;  // this thread's waits have timed out once
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full(s), 1);
+            // MODE_LUMI: the builder warps of every CTA of the pair arrive too
+            mbar_init(full(s), MODE == MODE_LUMI ? 1 + LB_WARPS * CL : 1);
             mbar_init(empty(s), 1);
         }
         for (int b = 0; b < 4; ++b) {
@@ -479,28 +509,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 const uint32_t st = base + s * stage_bytes;
+                // MODE_LUMI: only the B tiles are copied (the builders form A)
+                constexpr bool LOAD_A = MODE != MODE_LUMI;
+                const uint32_t tx = LOAD_A ? stage_bytes : T::NOPS * T::ATOMS * b_bytes;
                 if (CL == 2) {
                     const uint32_t fb = mapa(full(s), 0);
-                    if (leader) mbar_expect_tx(full(s), 2 * stage_bytes);
+                    if (leader) mbar_expect_tx(full(s), 2 * tx);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
                         const int x = koff + qk * T::KCS + a * T::KC;
-                        tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, arow);
+                        if (LOAD_A) tma_load_2d_pair(st + a * a_bytes, &mapA, fb, x, arow);
                         tma_load_2d_pair(st + offB + a * b_bytes, &mapB, fb, x, brow);
                         if (T::X3) {
-                            tma_load_2d_pair(st + offA2 + a * a_bytes, &mapA2, fb, x, arow);
+                            if (LOAD_A) tma_load_2d_pair(st + offA2 + a * a_bytes, &mapA2, fb, x, arow);
                             tma_load_2d_pair(st + offB2 + a * b_bytes, &mapB2, fb, x, brow);
                         }
                     }
                 } else {
-                    mbar_expect_tx(full(s), stage_bytes);
+                    mbar_expect_tx(full(s), tx);
 #pragma unroll
                     for (int a = 0; a < T::ATOMS; ++a) {
                         const int x = koff + qk * T::KCS + a * T::KC;
-                        tma_load_2d(st + a * a_bytes, &mapA, full(s), x, arow);
+                        if (LOAD_A) tma_load_2d(st + a * a_bytes, &mapA, full(s), x, arow);
                         tma_load_2d(st + offB + a * b_bytes, &mapB, full(s), x, brow);
                         if (T::X3) {
-                            tma_load_2d(st + offA2 + a * a_bytes, &mapA2, full(s), x, arow);
+                            if (LOAD_A) tma_load_2d(st + offA2 + a * a_bytes, &mapA2, full(s), x, arow);
                             tma_load_2d(st + offB2 + a * b_bytes, &mapB2, full(s), x, brow);
                         }
                     }
@@ -655,7 +688,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < 6) {
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;
         const int rl = quarter * 32 + lane;
@@ -705,7 +738,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int i = 0; i < MI; ++i) ps[i] = 0.f;
                 }
-                if constexpr (MODE == MODE_DENSE) {
+                if constexpr (MODE == MODE_DENSE || MODE == MODE_LUMI) {
                     // column col of the accumulator is data point nt * n_rows + col
                     const int dbase = nt * p.n_rows;
 #pragma unroll 1
@@ -728,7 +761,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // points >= nx (never written by the MMA) are skipped
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (MODE != MODE_DENSE && c * 64 < ncols) {
+                    if (MODE != MODE_DENSE && MODE != MODE_LUMI && c * 64 < ncols) {
                         uint32_t v[64];
                         tmem_ld64(taddr + (uint32_t)(c * 64), v);
 #pragma unroll
@@ -770,6 +803,131 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     }
+    if (MODE == MODE_LUMI && warp >= 6) {
+        // ------------------------------------------------ PDF matrix builders
+        // K runs over rows (c, i) of lnxp columns j (a power of two, at least
+        // 16, zero from j = nx), so a stage holds KCS / lnxp whole rows.
+        // Thread (m, h) forms A row m, columns j in [h, h + 1) * lnxp / 2 of
+        // every row of every stage: it keeps its f^r_{b_c}(x_j) in registers
+        // for the whole channel (reloaded when the channel changes) and loads
+        // one f^r_{a_c}(x_i) per row.  Values are rounded to the mode as the
+        // packing kernels round and written 16 bytes at a time at their place
+        // in the 128-byte swizzled K-major layout of the MMA descriptors.
+        const int bt = threadIdx.x - TC_THREADS;
+        const int m = bt & (TC_M - 1), h = bt >> 7;
+        const uint32_t m128 = (uint32_t)m * 128u, m7 = (uint32_t)(m & 7);
+        constexpr int CW = T::ESZ == 4 ? 4 : 8;  // columns per 16-byte chunk (8 chunks per atom row)
+        constexpr int JH_MAX = 32;               // columns per thread and row (lnxp <= 64)
+        const int jh = p.lnxp >> 1;
+        const int rows_s = T::KCS / p.lnxp;      // rows per stage
+        constexpr int RS_MAX = T::KCS / 16;      // rows per stage at most (lnxp >= 16)
+        float fbr[JH_MAX];
+#pragma unroll
+        for (int u = 0; u < JH_MAX; ++u) fbr[u] = 0.f;
+        int cur_c = -1;  // channel whose f_b values fbr holds
+        int it = 0;
+        bool ok = true;
+        for (int w = w_first; w < w_count && ok; w += w_step) {
+            int rt, nt, sp, pr;
+            tile_of(w, rt, nt, sp, pr);
+            const int koff = p.kbase + sp * p.kspl;
+            const float *FTr = p.FT + (size_t)rt * TC_M + m;
+            for (int q = 0; q < p.nchunks; ++q, ++it) {
+                const int s = it % S;
+                int got = 1;
+                if (lane == 0) got = mbar_wait(empty(s), ((it / S) & 1) ^ 1, dead);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t st = base + s * stage_bytes;
+                const int row0 = (koff + q * T::KCS) / p.lnxp;
+                // the f_a values of all the stage's rows are loaded first, so
+                // their latencies overlap
+                float fav[RS_MAX];
+                {
+                    int c = row0 / p.nx, i = row0 - (row0 / p.nx) * p.nx;
+#pragma unroll
+                    for (int ir = 0; ir < RS_MAX; ++ir) {
+                        fav[ir] = (ir < rows_s && c < p.lnc) ? __ldg(FTr + (size_t)(p.lfl[c] * p.nx + i) * p.R_pad)
+                                                             : 0.f;
+                        if (++i == p.nx) {
+                            i = 0;
+                            ++c;
+                        }
+                    }
+                }
+                int c = row0 / p.nx, i = row0 - (row0 / p.nx) * p.nx;
+#pragma unroll 1
+                for (int ir = 0; ir < rows_s; ++ir) {
+                    // this row's f_a, then the queue moves up one (constant indices)
+                    const float fa = fav[0];
+#pragma unroll
+                    for (int k = 0; k + 1 < RS_MAX; ++k) fav[k] = fav[k + 1];
+                    if (c < p.lnc && c != cur_c) {
+                        const float *fb = FTr + (size_t)(p.lfl[MAX_CH + c] * p.nx + h * jh) * p.R_pad;
+#pragma unroll
+                        for (int u = 0; u < JH_MAX; ++u)
+                            fbr[u] = (u < jh && h * jh + u < p.nx) ? __ldg(fb + (size_t)u * p.R_pad) : 0.f;
+                        cur_c = c;
+                    }
+                    // 16-byte chunks of this row owned by this thread: cs0, cs0 + 1, ...
+                    const int cs0 = (ir * p.lnxp + h * jh) / CW;
+#pragma unroll
+                    for (int cc = 0; cc < JH_MAX / CW; ++cc) {
+                        if (cc * CW < jh) {
+                            const int cs = cs0 + cc;
+                            const uint32_t addr = st + (uint32_t)(cs >> 3) * a_bytes + m128 +
+                                                  ((uint32_t)((cs & 7) ^ m7) << 4);
+                            if (T::ESZ == 4) {
+                                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                                             "r"(__float_as_uint(tf32_rna(fa * fbr[cc * CW]))),
+                                             "r"(__float_as_uint(tf32_rna(fa * fbr[cc * CW + 1]))),
+                                             "r"(__float_as_uint(tf32_rna(fa * fbr[cc * CW + 2]))),
+                                             "r"(__float_as_uint(tf32_rna(fa * fbr[cc * CW + CW - 1])))
+                                             : "memory");
+                            } else {
+                                // two values per conversion; lo = bf16(v - hi) from the same pair
+                                uint32_t hw[4], lw[4];
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const float v0 = fa * fbr[cc * CW + 2 * u], v1 = fa * fbr[cc * CW + 2 * u + 1];
+                                    const __nv_bfloat162 hp = __floats2bfloat162_rn(v0, v1);
+                                    hw[u] = *reinterpret_cast<const uint32_t *>(&hp);
+                                    if (T::X3) {
+                                        const __nv_bfloat162 lp =
+                                            __floats2bfloat162_rn(v0 - __low2float(hp), v1 - __high2float(hp));
+                                        lw[u] = *reinterpret_cast<const uint32_t *>(&lp);
+                                    }
+                                }
+                                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(hw[0]),
+                                             "r"(hw[1]), "r"(hw[2]), "r"(hw[3])
+                                             : "memory");
+                                if (T::X3)
+                                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr + offA2),
+                                                 "r"(lw[0]), "r"(lw[1]), "r"(lw[2]), "r"(lw[3])
+                                                 : "memory");
+                            }
+                        }
+                    }
+                    if (++i == p.nx) {
+                        i = 0;
+                        ++c;
+                    }
+                }
+                // the generic-proxy stores must be visible to the MMAs (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    if (CL == 2)
+                        mbar_arrive_cluster(mapa(full(s), 0));
+                    else
+                        mbar_arrive(full(s));
+                }
+            }
+        }
+    }
     tc_fence_before();
     if (CL == 2)
         cluster_sync();  // no MMA, commit, copy or arrive of the pair still targets this CTA
@@ -780,11 +938,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------ packing ----
-__device__ __forceinline__ float tf32_rna(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return __uint_as_float(r);
-}
 
 template <int PREC>
 __device__ __forceinline__ void store_op(long long idx, float v, __nv_bfloat16 *hi,
@@ -914,6 +1067,25 @@ __global__ void k_pack_dense(const double *__restrict__ fk, int ndata, long long
     }
 }
 
+// B operand of the dense formulation of a hadronic table from its FP64
+// table [ndata][nc][nx][nx]: row d holds data point d, column
+// k = (c * nx + i) * nxp + j holds FK[d][c][i][j] for j < nx and zero for the
+// padding j >= nx, columns past nc * nx * nxp and rows past ndata are zero.
+template <int PREC>
+__global__ void k_pack_lum(const double *__restrict__ fk, int ndata, int nc, int nx, int nxp, long long rows,
+                           int ktot_pad, __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+    const long long n = rows * ktot_pad;
+    const int nxnxp = nx * nxp;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long d = idx / ktot_pad;
+        const int k = (int)(idx % ktot_pad);
+        const int c = k / nxnxp, rem = k % nxnxp, i = rem / nxp, j = rem % nxp;
+        const float v = (d < ndata && c < nc && j < nx) ? (float)fk[((d * nc + c) * nx + i) * nx + j] : 0.f;
+        store_op<PREC>(idx, v, hi, lo, f32);
+    }
+}
+
 // Adjoint gather: gF[r][a][m] (+)= sum_t P1[t][g1(a)][i(m)][r] + sum_t P2[t][g2(a)][i(m)][r]
 // with i(m) the table's x index of grid point m, g1/g2 the groups of flavour a
 // in the forward and transposed packings (-1: none).  Grid (ceil(R / 128),
@@ -1030,7 +1202,7 @@ int opt_in_smem(K kernel, size_t bytes) {
 // Largest number of co-resident 2-CTA clusters of this kernel (cached per
 // kernel and shared-memory size); 0 if the query fails.
 template <typename K>
-int max_clusters(K kernel, size_t smem) {
+int max_clusters(K kernel, size_t smem, int threads) {
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> known;
     std::lock_guard<std::mutex> lock(mu);
@@ -1044,7 +1216,7 @@ int max_clusters(K kernel, size_t smem) {
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2 * 74, 1, 1);
-    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -1103,14 +1275,21 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
               const TcParams &p0, cudaStream_t s) {
     TcParams p = p0;
     // CTA pairs (256-row MMAs on two SMs) whenever the replica tiles pair up
-    if (p.nrt % 2 == 0) {
+    // and the channel groups span two stages or more on average.  A pair
+    // halves the B bytes each SM loads but adds cross-SM hand-offs per stage
+    // and per group; with groups of about one stage (config-2 shaped tables)
+    // single CTAs measured faster (BF16 forward 30.8 against 34.9 us), with
+    // long groups or one group pairs win (stress table BF16 1081 against 1030
+    // TFLOP/s, the Table 3 product 381 against 416 us).
+    const bool long_groups = p.ngroups == 1 || p.nchunks >= 2 * p.ngroups;
+    if (p.nrt % 2 == 0 && long_groups) {
         p.pwait = tc_pwait(p, tc_stages<PREC, 2>(), Tr<PREC>::KCS);
         auto kern = k_tc<PREC, G, MODE, 2>;
         const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(p.n_rows));
         // opt in once at the largest tile (n_rows = 256) so that every table fits
         int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 2>(256));
         if (rc) return rc;
-        const int nc = std::min(p.ntiles / 2, max_clusters(kern, smem));
+        const int nc = std::min(p.ntiles / 2, max_clusters(kern, smem, tc_threads<MODE>()));
         if (nc > 0) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -1119,7 +1298,7 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
             attr[0].val.clusterDim.y = 1;
             attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3(2 * nc, 1, 1);
-            cfg.blockDim = dim3(TC_THREADS, 1, 1);
+            cfg.blockDim = dim3(tc_threads<MODE>(), 1, 1);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
             cfg.attrs = attr;
@@ -1134,7 +1313,7 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
     int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;
     const int grid = std::min(p.ntiles, sm_count());
-    kern<<<grid, TC_THREADS, one_per_sm(tc_smem_bytes<PREC, 1>(p.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
+    kern<<<grid, tc_threads<MODE>(), one_per_sm(tc_smem_bytes<PREC, 1>(p.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
     count_launch();
     FK_CUDA(cudaGetLastError());
     return FK_OK;
@@ -1213,9 +1392,25 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     return FK_OK;
 }
 
+// O[r][d] = sum over splits sp (in order) of part[sp][r][d]
+__global__ void __launch_bounds__(256) k_dense_sum(const float *__restrict__ part, int nsplit, int ndata,
+                                                   int R, float *__restrict__ O, int ldo) {
+    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long n = (long long)R * ndata;
+    if (idx >= n) return;
+    float v = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) v += part[(size_t)sp * n + idx];
+    const long long r = idx / ndata, d = idx - r * ndata;
+    O[r * ldo + d] = v;
+}
+
+template <int PREC>
+int lum_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s);
+
 template <int PREC>
 int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
     const TcLayout &L = t->tc;
+    if (L.lum_on) return lum_tc_t<PREC>(t, F, R, O, ldo, s);
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     Scratch scr(s);
     float *Fm = nullptr;
@@ -1239,16 +1434,6 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
 // per extra split; ties keep fewer splits.  It depends on R (through the tile
 // count), so in these modes a replica's last bits can differ between calls
 // with different R.
-__global__ void __launch_bounds__(256) k_dense_sum(const float *__restrict__ part, int nsplit, int ndata,
-                                                   int R, float *__restrict__ O, int ldo) {
-    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
-    const long long n = (long long)R * ndata;
-    if (idx >= n) return;
-    float v = 0.f;
-    for (int sp = 0; sp < nsplit; ++sp) v += part[(size_t)sp * n + idx];
-    const long long r = idx / ndata, d = idx - r * ndata;
-    O[r * ldo + d] = v;
-}
 
 template <int PREC>
 int dense_tc_t(const fk_table *t, const float *Lm, int R, float *O, int ldo, cudaStream_t s) {
@@ -1290,6 +1475,71 @@ int dense_tc_t(const fk_table *t, const float *Lm, int R, float *O, int ldo, cud
         p.ldo = ldo;
     }
     rc = launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.fwd), p, s);
+    if (rc || nsplit == 1) return rc;
+    const long long n = (long long)R * t->ndata;
+    k_dense_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nsplit, t->ndata, R, O, ldo);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+// Forward in the dense formulation (MODE_LUMI): the builders' transposed
+// PDF rows FT[(a * nx + x) * R_pad + r] = f^r_a(x_x) (k_pack_fm through
+// lum_mmeta), one k_tc launch over (replica tile, data tile, K split) work
+// items with K split into fixed runs of LUMI_KSPLIT columns, and the
+// partial tiles added in split order (k_dense_sum) when there are several.
+template <int PREC>
+int lum_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const TcPack &pk = L.lum;
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    Scratch scr(s);
+    float *FT = nullptr;
+    FK_CUDA(scr.get(&FT, (size_t)NFL * t->nx * R_pad));
+    k_pack_fm<<<dim3((unsigned)(NFL * t->nx), (unsigned)((R_pad + 255) / 256)), 256, 0, s>>>(
+        L.lum_mmeta, F, NFL * t->nxg, R, R_pad, FT);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    TcParams p{};
+    p.npair = 1;  // pa = pb = 0
+    p.nrt = R_pad / TC_M;
+    p.ntile_n = pk.ntile_n;
+    p.n_rows = pk.n_rows;
+    p.nbl = pk.n_rows <= 128 ? 2 : 1;
+    p.ngroups = 1;
+    p.nx = t->nx;
+    p.ndata = t->ndata;
+    p.R = R;
+    p.R_pad = R_pad;
+    const int stages = pk.ktot_pad / Tr<PREC>::KCS;
+    const int cps = std::min(stages, LUMI_KSPLIT / Tr<PREC>::KCS);  // stages per split
+    const int nsplit = (stages + cps - 1) / cps;
+    p.nchunks = cps;
+    p.kbeg[0] = 0;
+    p.kend[0] = cps * Tr<PREC>::KCS;  // past K both operands read as zero
+    p.kspl = cps * Tr<PREC>::KCS;
+    p.nsplit = nsplit;
+    p.ntiles = p.nrt * pk.ntile_n * nsplit;
+    p.FT = FT;
+    for (int c = 0; c < t->nch; ++c) {
+        p.lfl[c] = (uint8_t)t->ca[c];
+        p.lfl[MAX_CH + c] = (uint8_t)t->cb[c];
+    }
+    p.lnc = t->nch;
+    p.lnxp = L.lum_nxp;
+    float *part = nullptr;
+    if (nsplit > 1) {
+        FK_CUDA(scr.get(&part, (size_t)nsplit * R * t->ndata));
+        p.O = part;
+        p.ldo = t->ndata;
+        p.ostride = (long long)R * t->ndata;
+    } else {
+        p.O = O;
+        p.ldo = ldo;
+    }
+    const BMaps mb = b_maps<PREC>(pk);
+    // the A maps are not read in this mode (the builders form A)
+    int rc = launch_tc<PREC, 16, MODE_LUMI>(t, *mb.b, *mb.b, mb, p, s);
     if (rc || nsplit == 1) return rc;
     const long long n = (long long)R * t->ndata;
     k_dense_sum<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nsplit, t->ndata, R, O, ldo);
@@ -1378,7 +1628,7 @@ void make_groups(const fk_table *t, const std::vector<int> &key, TcPack &pk) {
 
 }  // namespace
 
-int tc_build(fk_table *t, const double *host_fk) {
+int tc_build(fk_table *t, const double *host_fk, unsigned form) {
     TcLayout &L = t->tc;
     make_groups(t, t->ca, L.fwd);
     make_groups(t, t->cb, L.bwd);
@@ -1435,6 +1685,41 @@ int tc_build(fk_table *t, const double *host_fk) {
         t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
     }
 
+    // The paper's dense formulation with the PDF matrix formed on the chip
+    // (MODE_LUMI) for the forward, on request (FK_TABLE_LUMI).  It is not
+    // chosen by default: forming the operand takes 16K FP32 products,
+    // conversions and 32 KB of shared-memory stores per 1.3k-cycle MMA stage
+    // on the SM's issue slots, and the builders stay about four times behind
+    // the tensor cores (config 2, BF16: 87 us against 31 us factorised).  A
+    // table property: a replica's result does not depend on R.
+    L.lum_nxp = 16;
+    while (L.lum_nxp < t->nx) L.lum_nxp *= 2;
+    const long long Kl = (long long)t->nch * t->nx * L.lum_nxp;
+    L.lum_on = form == FK_TABLE_LUMI;
+    if (L.lum_on) {
+        TcPack &pk = L.lum;
+        pk.n_rows = std::min(256, (t->ndata + 15) / 16 * 16);
+        pk.ntile_n = (t->ndata + pk.n_rows - 1) / pk.n_rows;
+        pk.grp = TcGroups{};
+        pk.grp.ngroups = 1;
+        pk.grp.kbeg[0] = 0;
+        pk.grp.kend[0] = (int)((Kl + KPAD - 1) / KPAD * KPAD);
+        pk.ktot = pk.grp.kend[0];
+        const int kal = (t->mask & (FK_PREC_BIT(FK_BF16) | FK_PREC_BIT(FK_TF32))) ? 128 : 64;
+        pk.ktot_pad = (pk.ktot + kal - 1) / kal * kal;
+        const size_t elems = (size_t)pk.ntile_n * pk.n_rows * pk.ktot_pad;
+        if ((want_hi && cudaMalloc(&pk.hi, elems * 2)) || (want_lo && cudaMalloc(&pk.lo, elems * 2)) ||
+            (want_f32 && cudaMalloc(&pk.f32, elems * 4)))
+            return fail(FK_ENOMEM, "tensor-core table storage");
+        t->bytes += elems * (2 * want_hi + 2 * want_lo + 4 * want_f32);
+        std::vector<int> mm((size_t)NFL * t->nx);
+        for (int a = 0; a < NFL; ++a)
+            for (int x = 0; x < t->nx; ++x) mm[(size_t)a * t->nx + x] = a * t->nxg + t->xmap[x];
+        if (cudaMalloc(&L.lum_mmeta, mm.size() * sizeof(int))) return fail(FK_ENOMEM, "tensor-core gather maps");
+        FK_CUDA(cudaMemcpy(L.lum_mmeta, mm.data(), mm.size() * sizeof(int), cudaMemcpyHostToDevice));
+        t->bytes += mm.size() * sizeof(int);
+    }
+
     // full FP64 copy on the device for the packing kernels, then freed
     double *owned = nullptr;
     cudaStream_t s = nullptr;
@@ -1453,6 +1738,23 @@ int tc_build(fk_table *t, const double *host_fk) {
         if (!rc && want_lo) rc = pack_table<FK_BF16X3>(t, pk, tr, owned, s);
         else if (!rc && want_hi) rc = pack_table<FK_BF16>(t, pk, tr, owned, s);
     }
+    if (!rc && L.lum_on) {
+        const TcPack &pk = L.lum;
+        const long long rows = (long long)pk.ntile_n * pk.n_rows;
+        const unsigned blocks = (unsigned)std::min<long long>((rows * pk.ktot_pad + 255) / 256, 148LL * 32);
+        if (want_f32)
+            k_pack_lum<FK_TF32><<<blocks, 256, 0, s>>>(owned, t->ndata, t->nch, t->nx, L.lum_nxp, rows, pk.ktot_pad,
+                                                      pk.hi, pk.lo, pk.f32);
+        if (want_lo)
+            k_pack_lum<FK_BF16X3><<<blocks, 256, 0, s>>>(owned, t->ndata, t->nch, t->nx, L.lum_nxp, rows,
+                                                        pk.ktot_pad, pk.hi, pk.lo, pk.f32);
+        else if (want_hi)
+            k_pack_lum<FK_BF16><<<blocks, 256, 0, s>>>(owned, t->ndata, t->nch, t->nx, L.lum_nxp, rows, pk.ktot_pad,
+                                                      pk.hi, pk.lo, pk.f32);
+        count_launch();
+        e = cudaGetLastError();
+        if (e) rc = cuda_fail(e, "tensor-core table packing");
+    }
     if (!rc) {
         e = cudaStreamSynchronize(s);
         if (e) rc = cuda_fail(e, "tensor-core table packing");
@@ -1469,6 +1771,20 @@ int tc_build(fk_table *t, const double *host_fk) {
         if (want_hi && (rc = make_map(&pk->half_hi, pk->hi, 2, pk->ktot_pad, rows, h))) return rc;
         if (want_lo && (rc = make_map(&pk->half_lo, pk->lo, 2, pk->ktot_pad, rows, h))) return rc;
         if (want_f32 && (rc = make_map(&pk->half_f32, pk->f32, 4, pk->ktot_pad, rows, h))) return rc;
+    }
+    if (L.lum_on) {
+        TcPack &pk = L.lum;
+        const long long lrows = (long long)pk.ntile_n * pk.n_rows;
+        const int h = pk.n_rows / 2;
+        if (want_hi && ((rc = make_map(&pk.map_hi, pk.hi, 2, pk.ktot_pad, lrows, pk.n_rows)) ||
+                        (rc = make_map(&pk.half_hi, pk.hi, 2, pk.ktot_pad, lrows, h))))
+            return rc;
+        if (want_lo && ((rc = make_map(&pk.map_lo, pk.lo, 2, pk.ktot_pad, lrows, pk.n_rows)) ||
+                        (rc = make_map(&pk.half_lo, pk.lo, 2, pk.ktot_pad, lrows, h))))
+            return rc;
+        if (want_f32 && ((rc = make_map(&pk.map_f32, pk.f32, 4, pk.ktot_pad, lrows, pk.n_rows)) ||
+                         (rc = make_map(&pk.half_f32, pk.f32, 4, pk.ktot_pad, lrows, h))))
+            return rc;
     }
     return FK_OK;
 }
@@ -1710,6 +2026,14 @@ void tc_free(fk_table *t) {
     }
     cudaFree(t->tc.gmap);
     t->tc.gmap = nullptr;
+    fk::TcPack &lum = t->tc.lum;
+    cudaFree(lum.hi);
+    cudaFree(lum.lo);
+    cudaFree(lum.f32);
+    lum.hi = lum.lo = nullptr;
+    lum.f32 = nullptr;
+    cudaFree(t->tc.lum_mmeta);
+    t->tc.lum_mmeta = nullptr;
 }
 
 namespace {

@@ -135,6 +135,11 @@ size_t request_device_bytes(const fk_table *t, int R, int prec) {
         // PDF matrix (hadronic) and up to 1 GiB of exact partial tiles
         const size_t rpad = (size_t)(R + 127) / 128 * 128;
         b += rpad * t->tc.oz.ktot_pad * 16 + (t->kind == FK_KIND_HAD ? 8 * (size_t)R * t->E : 0) + (1ull << 30);
+    } else if (t->tc.lum_on) {
+        // the builders' transposed PDF rows and the partial tiles of the K splits
+        const size_t rpad = (size_t)(R + 127) / 128 * 128;
+        const size_t nsplit = (size_t)(t->tc.lum.ktot_pad + 1535) / 1536;
+        b += 4 * rpad * NFL * t->nx + 4 * nsplit * R * t->ndata;
     } else {
         const size_t rpad = (size_t)(R + 127) / 128 * 128;
         b += rpad * t->tc.fwd.ktot_pad * (prec == FK_TF32 ? 4 : (prec == FK_BF16X3 ? 4 : 2)) +

@@ -107,3 +107,22 @@ def test_debug_build_exports_and_release_reports_no_debug():
     assert lib.fk_debug_status(0, ctypes.byref(code), ctypes.byref(idx)) == _lib.FK_EUNSUPPORTED
     assert code.value == 0 and idx.value == 0
     assert lib.fk_debug_selftest() == _lib.FK_EUNSUPPORTED
+
+
+def test_form_flags_are_checked_on_the_host():
+    """FK_TABLE_FACTORED and FK_TABLE_LUMI: at most one, hadronic tables only
+    (rejected before any device work)."""
+    import numpy as np
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    fkv = np.zeros((1, 1, 3, 3))
+    ca, cb = np.zeros(1, np.int32), np.ones(1, np.int32)
+    both = (1 << _lib.FK_FP32) | _lib.FK_TABLE_FACTORED | _lib.FK_TABLE_LUMI
+    assert lib.fk_table_create_had(fkv.ctypes.data, 1, ca.ctypes.data, cb.ctypes.data, 1, 3, None, 3, both,
+                                   ctypes.byref(out)) == _lib.FK_EINVAL
+    fd, flav = np.zeros((1, 1, 3)), np.zeros(1, np.int32)
+    assert lib.fk_table_create_dis(fd.ctypes.data, 1, flav.ctypes.data, 1, 3, None, 3,
+                                   (1 << _lib.FK_FP32) | _lib.FK_TABLE_LUMI, ctypes.byref(out)) == _lib.FK_EINVAL
+    with pytest.raises(ValueError):
+        fk.Table.from_workload(type("D", (), {"compact": lambda s: fd, "flav": flav, "xmap": None, "nxg": 3})(),
+                               precs=("fp32",), form="lumi")

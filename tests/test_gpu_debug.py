@@ -3,7 +3,8 @@
 Index checks in the kernels record the first failed check and skip the
 access; per-call scratch buffers carry guard bytes verified when they are
 released.  A child process loads the debug build, runs every path (hadronic
-and DIS forward and adjoint in all modes, the dense product, chi^2) on the
+and DIS forward and adjoint in all modes, the hadronic forward's dense form,
+the dense product, chi^2) on the
 shapes nx = 1, 17, 33, ndata = 1, 129, one channel, R = 1, 3, 257, compares
 with the FP64 oracle and then requires fk_debug_status to report no failed
 check; fk_debug_selftest shows that a failed check is reported.
@@ -42,6 +43,17 @@ for (nd, nc, nx, R) in [(1, 1, 1, 1), (129, 1, 17, 3), (1, 5, 33, 257), (129, 3,
             g = fk.conv_backward(tab, Fd, torch.tensor(gO, dtype=dt, device="cuda"), prec).double().cpu().numpy()
             assert np.all(np.isfinite(g))
             worst = max(worst, err)
+# the dense form of the hadronic forward (PDF matrix built in shared memory)
+for (nd, nc, nx, R) in [(1, 1, 1, 1), (129, 3, 17, 3), (300, 5, 33, 257)]:
+    rng = np.random.default_rng(nd + nc + nx + R + 1)
+    x = W.xgrid(nx, 1e-6)
+    F = W.pdf_replicas(x, W.pdf_params(rng), R, rng)
+    t = W.had_table(rng, nd, nc, x)
+    O_ref, S = oracle.conv(t, F)
+    for prec in ("bf16", "bf16x3", "tf32"):
+        tab = fk.Table.from_workload(t, precs=(prec,), form="lumi")
+        O = fk.conv(tab, torch.tensor(F, dtype=torch.float32, device="cuda"), prec).double().cpu().numpy()
+        assert (np.abs(O - O_ref) / S).max() <= tol[prec] + 1600 * 2.0 ** -24, (nd, nc, nx, R, prec)
 L = np.random.default_rng(1).standard_normal((3, 300))
 fkd = np.random.default_rng(2).standard_normal((129, 300))
 O_ref, S = oracle.dense(fkd, L)

@@ -470,6 +470,11 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
         __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // Launched as a programmatic dependent of the previous kernel in the
+    // stream (the operand packing): the set-up above ran while that kernel
+    // finished; nothing it writes is read, and nothing is written, before
+    // this wait for its completion.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     // groups whose accumulator hand-off the producer takes (tc_pwait)
     const uint32_t pwait = p.pwait;
@@ -996,6 +1001,9 @@ template <int PREC>
 __global__ void __launch_bounds__(256) k_pack_pdf(const int *__restrict__ kmeta, int ktot_pad,
                                                   const float *__restrict__ F, int frow, int R, int R_pad,
                                                   __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+    // the tensor-core kernel that follows may start its set-up now (it waits
+    // for this grid's completion before reading what it writes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int k0 = (blockIdx.x * 256 + threadIdx.x) * 8;
     if (k0 >= ktot_pad) return;
     int o[8];
@@ -1008,6 +1016,43 @@ __global__ void __launch_bounds__(256) k_pack_pdf(const int *__restrict__ kmeta,
         for (int u = 0; u < 8; ++u)
             v[u] = (r < R && o[u] >= 0 && FK_DBG(o[u] < frow, 10, o[u])) ? __ldg(Fr + o[u]) : 0.f;
         if (FK_DBG(r < R_pad && k0 + 8 <= ktot_pad, 11, k0)) store8<PREC>((size_t)r * ktot_pad + k0, v, hi, lo, f32);
+    }
+}
+
+// The forward's two packings in one launch: blocks [0, nk * ny) pack the A
+// operand as k_pack_pdf does (column chunk blockIdx.x % nk, rows from
+// blockIdx.x / nk strided by ny), the blocks after them the epilogue
+// multipliers Fm[m][r] as k_pack_fm does (m = b % nm, replicas
+// (b / nm) * 256 + thread).
+template <int PREC>
+__global__ void __launch_bounds__(256) k_pack_fwd(const int *__restrict__ kmeta, int ktot_pad,
+                                                  const float *__restrict__ F, int frow, int R, int R_pad,
+                                                  __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32, int nk, int ny,
+                                                  const int *__restrict__ mmeta, int nm, float *__restrict__ Fm) {
+    // the tensor-core kernel that follows may start its set-up now (it waits
+    // for this grid's completion before reading what it writes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int b = blockIdx.x;
+    if (b < nk * ny) {
+        const int k0 = ((b % nk) * 256 + threadIdx.x) * 8;
+        if (k0 >= ktot_pad) return;
+        int o[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) o[u] = __ldg(kmeta + k0 + u);
+        for (int r = b / nk; r < R_pad; r += ny) {
+            const float *Fr = F + (size_t)r * frow;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (r < R && o[u] >= 0 && FK_DBG(o[u] < frow, 10, o[u])) ? __ldg(Fr + o[u]) : 0.f;
+            if (FK_DBG(k0 + 8 <= ktot_pad, 11, k0)) store8<PREC>((size_t)r * ktot_pad + k0, v, hi, lo, f32);
+        }
+    } else {
+        const int e = b - nk * ny, m = e % nm;
+        const int r = (e / nm) * 256 + threadIdx.x;
+        if (r >= R_pad) return;
+        const int o = __ldg(mmeta + m);
+        Fm[(size_t)m * R_pad + r] = r < R ? __ldg(F + (size_t)r * frow + o) : 0.f;
     }
 }
 
@@ -1292,17 +1337,19 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
         const int nc = std::min(p.ntiles / 2, max_clusters(kern, smem, tc_threads<MODE>()));
         if (nc > 0) {
             cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
+            cudaLaunchAttribute attr[2];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = 2;
             attr[0].val.clusterDim.y = 1;
             attr[0].val.clusterDim.z = 1;
+            attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[1].val.programmaticStreamSerializationAllowed = 1;
             cfg.gridDim = dim3(2 * nc, 1, 1);
             cfg.blockDim = dim3(tc_threads<MODE>(), 1, 1);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
             cfg.attrs = attr;
-            cfg.numAttrs = 1;
+            cfg.numAttrs = 2;
             FK_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mA2, *mb.h, *mb.h2, p));
             count_launch();
             return FK_OK;
@@ -1313,9 +1360,18 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
     int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;
     const int grid = std::min(p.ntiles, sm_count());
-    kern<<<grid, tc_threads<MODE>(), one_per_sm(tc_smem_bytes<PREC, 1>(p.n_rows)), s>>>(mA, mA2, *mb.b, *mb.b2, p);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(tc_threads<MODE>(), 1, 1);
+    cfg.dynamicSmemBytes = one_per_sm(tc_smem_bytes<PREC, 1>(p.n_rows));
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FK_CUDA(cudaLaunchKernelEx(&cfg, kern, mA, mA2, *mb.b, *mb.b2, p));
     count_launch();
-    FK_CUDA(cudaGetLastError());
     return FK_OK;
 }
 
@@ -1353,16 +1409,19 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
     // A rows: the PDF grid of a replica, or a dense table's PDF matrix row
     // (or, when given, rows of frow_in elements: the adjoint's gO)
     const int frow = frow_in >= 0 ? frow_in : t->kind == FK_KIND_DENSE ? (int)t->E : NFL * t->nxg;
-    k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
-                       s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
+    if (Fm) {
+        // the forward: A operand and epilogue multipliers in one launch
+        const int nk = (pk.ktot_pad + 2047) / 2048, ny = std::min(R_pad, 4096);
+        const int nm = pk.grp.ngroups * t->nx;
+        const long long blocks = (long long)nk * ny + (long long)nm * ((R_pad + 255) / 256);
+        k_pack_fwd<PREC><<<(unsigned)blocks, 256, 0, s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32, nk,
+                                                          ny, pk.mmeta, nm, Fm);
+    } else {
+        k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
+                           s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
+    }
     count_launch();
     FK_CUDA(cudaGetLastError());
-    if (Fm) {
-        k_pack_fm<<<dim3((unsigned)(pk.grp.ngroups * t->nx), (unsigned)((R_pad + 255) / 256)), 256, 0, s>>>(
-            pk.mmeta, F, frow, R, R_pad, Fm);
-        count_launch();
-        FK_CUDA(cudaGetLastError());
-    }
     const int esz = Tr<PREC>::ESZ;
     int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
     if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);

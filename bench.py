@@ -692,10 +692,25 @@ def run_peaks(args):
             fl = 2.0 * 8 * iters * 256 * blocks
             res[f"{name}_tflops"], res[f"{name}_tflops_sustained"] = rate(
                 lambda: lib.fk_fma_probe(prec, blocks, iters, ctypes.c_void_p(sink.data_ptr()), stream), fl)
+        # cycles one BF16 tcgen05.mma (M = 128, K = 16) takes, by N: best of 5 runs of 4096
+        cyc = torch.zeros(1, dtype=torch.int64, device="cuda")
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        for fill, key in ((1, "tcgen05_f16_mma_cycles_by_n"), (0, "tcgen05_f16_mma_cycles_by_n_zero_operands")):
+            per = {}
+            for n in (64, 128, 192, 240, 256):
+                best = None
+                for _ in range(5):
+                    _lib.call("fk_mma_probe", n, 4096, fill, ctypes.c_void_p(cyc.data_ptr()), stream)
+                    torch.cuda.synchronize()
+                    v = cyc.item() / 4096
+                    best = v if best is None else min(best, v)
+                per[str(n)] = round(best, 1)
+            res[key] = per
     res["clocks"] = clk.summary()
     res["how"] = ("TF32: torch.matmul fp32 8192^3 with TF32 allowed (cuBLAS), 2 N^3 flops; FP32 / FP64: "
                   "fk_fma_probe, 8 independent FMA chains per thread, 8 x SMs CTAs of 256 threads; best of 10 "
-                  "(burst) and back to back for 4 s (sustained), CUDA events")
+                  "(burst) and back to back for 4 s (sustained), CUDA events; MMA cycles: fk_mma_probe, one CTA, "
+                  "4096 back-to-back BF16 tcgen05.mma of 128 x N x 16, SM cycles per instruction, best of 5")
     print(json.dumps(res), flush=True)
 
 

@@ -398,6 +398,19 @@ int fk_adam_step(void *p, const void *g, void *m, void *v, long long n, int t, d
  */
 int fk_fma_probe(int prec, int blocks, int iters, void *sink, fk_stream stream);
 
+/*
+ * Tensor-core issue probe: one CTA issues `iters` BF16 tcgen05.mma
+ * instructions of M = 128, N = n, K = 16 back to back (shared-memory operands
+ * of zeros (fill = 0) or of finite values of varying sign, exponent and
+ * mantissa (fill = 1), one TMEM accumulator) and writes the SM cycles from
+ * the first issue to the completion of the last to cycles[0] (DEVICE, one
+ * unsigned long long; 0 if the bounded wait ran out).  Used to measure the
+ * cycles one instruction takes as a function of N.  Asynchronous on stream.
+ * Errors: FK_EINVAL (n not a multiple of 16 in 16..256, iters outside
+ * 1..2^24, fill not 0 or 1, cycles NULL), FK_ECUDA.
+ */
+int fk_mma_probe(int n, int iters, int fill, unsigned long long *cycles, fk_stream stream);
+
 /* -------------------------------------------------------------- serving */
 
 /*

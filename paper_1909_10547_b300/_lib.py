@@ -40,6 +40,7 @@ SIGNATURES = {
     "fk_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                      ctypes.c_double, I, P],
     "fk_fma_probe": [I, I, I, P, P],
+    "fk_mma_probe": [I, I, I, P, P],
     "fk_serve_create": [SZ, I, PP],
     "fk_serve_add_table": [P, P, P],
     "fk_serve_submit": [P, I, P, I, I, ctypes.POINTER(U64)],

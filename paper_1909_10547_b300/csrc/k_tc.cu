@@ -2096,6 +2096,64 @@ void tc_free(fk_table *t) {
 }
 
 namespace {
+// Tensor-core issue probe (fk_mma_probe): one CTA, one thread issues `iters`
+// BF16 tcgen05.mma instructions of 128 x n x 16 back to back from a 128-byte
+// swizzled operand pair in shared memory (zeros, or with fill = 1 finite
+// values of varying sign, exponent and mantissa) into one TMEM accumulator,
+// commits them to an mbarrier and waits (bounded); the clock64 interval from
+// the first issue to the commit's arrival, in SM cycles, goes to cycles[0].
+__global__ void __launch_bounds__(64, 1) k_mma_probe(int n, int iters, int fill, unsigned long long *cycles) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)n * 128;
+    const uint32_t bar = base + a_bytes + b_bytes;
+    volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(smem_raw + (bar - raw) + 16);
+    const int warp = threadIdx.x >> 5;
+    for (uint32_t o = threadIdx.x * 16u; o < a_bytes + b_bytes; o += 64u * 16u) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            // two BF16 values per word: |v| in [2^-4, 2^4), both signs
+            const uint32_t h = (o + 4u * u) * 2654435761u;
+            const uint32_t v0 = ((h >> 31) << 15) | ((123u + ((h >> 8) & 7u)) << 7) | (h & 0x7Fu);
+            const uint32_t v1 = (((h >> 30) & 1u) << 15) | ((123u + ((h >> 12) & 7u)) << 7) | ((h >> 16) & 0x7Fu);
+            w[u] = fill ? (v0 | (v1 << 16)) : 0u;
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + o), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                     "r"(w[3])
+                     : "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc<1>(smem_u32((const void *)slot));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    if (threadIdx.x == 32) {
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        const uint32_t a0 = desc_lo(base), b0 = desc_lo(base + a_bytes);
+        bool dead = false;
+        const unsigned long long t0 = clock64();
+        for (int i = 0; i < iters; ++i) {
+            const uint32_t off = (uint32_t)(i & 3) * 2u;  // the four K steps of the swizzle atom
+            mma<FK_BF16, 1>(tmem, desc64(a0 + off), desc64(b0 + off), idesc, 1);
+        }
+        mma_commit<1>(bar);
+        mbar_wait(bar, 0, dead);
+        cycles[0] = dead ? 0ull : clock64() - t0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_free<1>(tmem);
+}
+
 // One thread waits on an mbarrier that expects one arrival nobody makes: the
 // bounded wait gives up after limit_ns and raises the device error word.
 __global__ void k_wait_selftest(uint64_t limit_ns) {
@@ -2107,6 +2165,15 @@ __global__ void k_wait_selftest(uint64_t limit_ns) {
     mbar_wait(b, 0, dead, limit_ns);
 }
 }  // namespace
+
+int mma_probe(int n, int iters, int fill, unsigned long long *cycles, cudaStream_t s) {
+    const size_t smem = 1024 + (size_t)TC_M * 128 + (size_t)n * 128 + 256;
+    FK_CUDA(cudaFuncSetAttribute(k_mma_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_per_sm(smem)));
+    k_mma_probe<<<1, 64, one_per_sm(smem), s>>>(n, iters, fill, cycles);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
 
 int make_plain_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_cols,
                    int box_rows) {
@@ -2137,6 +2204,14 @@ int device_status(int reset) {
 }
 
 }  // namespace fk
+
+int fk_mma_probe(int n, int iters, int fill, unsigned long long *cycles, fk_stream stream) {
+    using namespace fk;
+    if (n < 16 || n > 256 || n % 16 || iters < 1 || iters > (1 << 24) || (fill != 0 && fill != 1) || !cycles)
+        return fail(FK_EINVAL,
+                    "fk_mma_probe: n a multiple of 16 in 16..256, iters in 1..2^24, fill 0 or 1, cycles not NULL");
+    return mma_probe(n, iters, fill, cycles, (cudaStream_t)stream);
+}
 
 int fk_wait_selftest(int limit_us) {
     using namespace fk;

@@ -126,3 +126,13 @@ def test_form_flags_are_checked_on_the_host():
     with pytest.raises(ValueError):
         fk.Table.from_workload(type("D", (), {"compact": lambda s: fd, "flav": flav, "xmap": None, "nxg": 3})(),
                                precs=("fp32",), form="lumi")
+
+
+def test_probe_argument_errors_need_no_gpu():
+    lib = _lib.load()
+    assert lib.fk_mma_probe(8, 10, 0, ctypes.c_void_p(1), None) == _lib.FK_EINVAL     # n not a multiple of 16
+    assert lib.fk_mma_probe(272, 10, 0, ctypes.c_void_p(1), None) == _lib.FK_EINVAL   # n > 256
+    assert lib.fk_mma_probe(64, 0, 0, ctypes.c_void_p(1), None) == _lib.FK_EINVAL     # iters < 1
+    assert lib.fk_mma_probe(64, 10, 2, ctypes.c_void_p(1), None) == _lib.FK_EINVAL    # fill not 0 or 1
+    assert lib.fk_mma_probe(64, 10, 0, None, None) == _lib.FK_EINVAL                  # no output
+    assert lib.fk_fma_probe(_lib.FK_BF16, 1, 1, ctypes.c_void_p(1), None) == _lib.FK_EINVAL

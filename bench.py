@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serve case: number of requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve case: arrivals per second")
     ap.add_argument("--ndata", type=int, default=2000, help="stress case: data points")
+    ap.add_argument("--form", default="factored", choices=["factored", "lumi"],
+                    help="stress case, reduced modes: the hadronic forward's formulation (FK_TABLE_LUMI)")
     ap.add_argument("--table", default="stress", choices=["stress", "config1"],
                     help="stress case: the stress table, or the plain hadronic table of configs 1-2 "
                          "(200 data points, 60 channels, nx = 30; R = 512 is config 2)")
@@ -965,7 +967,10 @@ def run_stress(args):
         x = W.xgrid(50, 1e-7)
         F = W.pdf_replicas(x, W.pdf_params(np.random.default_rng(1)), R, np.random.default_rng(2) if R > 1 else None)
         name = f"hadronic stress table {args.ndata} x 196 channels x 50 x 50, one convolution, R={R}"
-    tab = fk.Table.from_workload(t, precs=(args.prec,))
+    lumi = args.form == "lumi" and args.prec in ("bf16", "bf16x3", "tf32")
+    tab = fk.Table.from_workload(t, precs=(args.prec,), form="lumi" if lumi else None)
+    if lumi:
+        name += ", dense form (PDF matrix formed in shared memory)"
     dt = torch.float64 if args.prec in ("fp64", "fp64tc") else torch.float32
     Fd = torch.tensor(F, dtype=dt, device="cuda")
     O = fk.conv(tab, Fd, args.prec)

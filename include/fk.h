@@ -33,6 +33,12 @@
  *    before it completes.  Input buffers must stay valid, and outputs must not
  *    be read, until the stream has reached that point.  Temporary device
  *    memory comes from CUDA's stream-ordered allocator on the same stream.
+ *    The first table created configures the device's default memory pool:
+ *    freed memory stays in the pool (release threshold at its maximum), and
+ *    a block freed on one stream is reused on another only once its free is
+ *    known complete through event dependencies (opportunistic reuse and
+ *    internal dependencies off), so that after work spread over many
+ *    streams an allocation costs no more host time than before.
  *  - Argument errors are detected on the host before anything is enqueued:
  *    such a call returns FK_EINVAL and enqueues nothing.
  */

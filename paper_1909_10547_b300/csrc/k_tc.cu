@@ -991,20 +991,35 @@ __device__ __forceinline__ void store8(size_t at, const float (&v)[8], __nv_bflo
     }
 }
 
+// One A operand packing to fill: its column map, padded width, column chunks
+// of 2048 (nk) and destination copies.
+struct PackDst {
+    const int *kmeta;
+    int ktot_pad, nk;
+    __nv_bfloat16 *hi, *lo;
+    float *f32;
+};
+
 // A operand A[r][k] = f^r_{o_c}(x_j) for k = (channel c of its group, j), where
 // o_c is the channel's other flavour (b_c for the forward packing, a_c for the
-// transposed one), gathered through kmeta.  Grid (ceil(ktot_pad / 2048),
-// min(R_pad, 65535)), rows r strided by the grid height: 8 consecutive K
+// transposed one), gathered through kmeta.  One launch fills one packing
+// (d1.nk = 0) or two (the adjoint's forward and transposed packings):
+// grid (d0.nk + d1.nk, min(R_pad, 65535)), column chunk blockIdx.x of d0, or
+// blockIdx.x - d0.nk of d1; rows r strided by the grid height: 8 consecutive K
 // columns per thread, one 16-byte store per operand copy (ktot_pad is a
 // multiple of 64).
 template <int PREC>
-__global__ void __launch_bounds__(256) k_pack_pdf(const int *__restrict__ kmeta, int ktot_pad,
-                                                  const float *__restrict__ F, int frow, int R, int R_pad,
-                                                  __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *f32) {
+__global__ void __launch_bounds__(256) k_pack_pdf(const PackDst d0, const PackDst d1,
+                                                  const float *__restrict__ F, int frow, int R, int R_pad) {
     // the tensor-core kernel that follows may start its set-up now (it waits
     // for this grid's completion before reading what it writes)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int k0 = (blockIdx.x * 256 + threadIdx.x) * 8;
+    const bool second = (int)blockIdx.x >= d0.nk;
+    const int *kmeta = second ? d1.kmeta : d0.kmeta;
+    const int ktot_pad = second ? d1.ktot_pad : d0.ktot_pad;
+    __nv_bfloat16 *hi = second ? d1.hi : d0.hi, *lo = second ? d1.lo : d0.lo;
+    float *f32 = second ? d1.f32 : d0.f32;
+    const int k0 = (((int)blockIdx.x - (second ? d0.nk : 0)) * 256 + threadIdx.x) * 8;
     if (k0 >= ktot_pad) return;
     int o[8];
 #pragma unroll
@@ -1391,11 +1406,24 @@ int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2
     return fail(FK_EINVAL, "bad tile height");
 }
 
+// k_pack_pdf over one packing (d1.nk = 0) or two, in one launch.
+template <int PREC>
+cudaError_t launch_pack(const PackDst &d0, const PackDst &d1, const float *F, int frow, int R, int R_pad,
+                        cudaStream_t s) {
+    k_pack_pdf<PREC><<<dim3((unsigned)(d0.nk + d1.nk), (unsigned)std::min(R_pad, 65535)), 256, 0, s>>>(
+        d0, d1, F, frow, R, R_pad);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // Packs the A operand (and, if Fm is not NULL, the forward multipliers) for one
 // packing of the table, builds its tensor maps and fills the common params.
+// With defer (and no Fm) the A packing is described in *defer instead of
+// launched: the caller launches it, possibly together with another.
 template <int PREC>
 int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch &scr, float *Fm,
-            cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p, int frow_in = -1) {
+            cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p, int frow_in = -1,
+            PackDst *defer = nullptr) {
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float *f32 = nullptr;
@@ -1416,12 +1444,16 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
         const long long blocks = (long long)nk * ny + (long long)nm * ((R_pad + 255) / 256);
         k_pack_fwd<PREC><<<(unsigned)blocks, 256, 0, s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32, nk,
                                                           ny, pk.mmeta, nm, Fm);
+        count_launch();
+        FK_CUDA(cudaGetLastError());
     } else {
-        k_pack_pdf<PREC><<<dim3((unsigned)((pk.ktot_pad + 2047) / 2048), (unsigned)std::min(R_pad, 65535)), 256, 0,
-                           s>>>(pk.kmeta, pk.ktot_pad, F, frow, R, R_pad, hi, lo, f32);
+        const PackDst d{pk.kmeta, pk.ktot_pad, (pk.ktot_pad + 2047) / 2048, hi, lo, f32};
+        if (defer) {
+            *defer = d;  // the caller launches it, with another packing
+        } else {
+            FK_CUDA(launch_pack<PREC>(d, PackDst{}, F, frow, R, R_pad, s));
+        }
     }
-    count_launch();
-    FK_CUDA(cudaGetLastError());
     const int esz = Tr<PREC>::ESZ;
     int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
     if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);
@@ -1610,7 +1642,7 @@ int lum_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
 // Adjoint: term 1 (derivative with respect to the first flavour of each
 // channel) from the forward packing, term 2 (second flavour) from the
 // transposed packing, both as per-tile partial sums, then one fixed-order
-// gather into gF.
+// gather into gF.  Both A operands are packed by one launch.
 template <int PREC>
 int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
              int accumulate, cudaStream_t s) {
@@ -1622,15 +1654,19 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
     FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
     const TcPack *packs[2] = {&L.fwd, &L.bwd};
     float *parts[2] = {P1, P2};
+    CUtensorMap mA[2], mA2[2];
+    TcParams p[2];
+    PackDst pd[2];
     for (int k = 0; k < 2; ++k) {
-        CUtensorMap mA, mA2;
-        TcParams p;
-        int rc = prepare<PREC>(t, *packs[k], F, R, scr, nullptr, s, mA, mA2, p);
+        const int rc = prepare<PREC>(t, *packs[k], F, R, scr, nullptr, s, mA[k], mA2[k], p[k], -1, &pd[k]);
         if (rc) return rc;
-        p.ldo = ldgo;
-        p.gO = gO;
-        p.P = parts[k];
-        rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, *packs[k], p, s);
+    }
+    FK_CUDA(launch_pack<PREC>(pd[0], pd[1], F, NFL * t->nxg, R, R_pad, s));
+    for (int k = 0; k < 2; ++k) {
+        p[k].ldo = ldgo;
+        p[k].gO = gO;
+        p[k].P = parts[k];
+        const int rc = launch_tc_g<PREC, MODE_ADJ>(t, mA[k], mA2[k], *packs[k], p[k], s);
         if (rc) return rc;
     }
     k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(

@@ -41,6 +41,11 @@ REPLICAS = 100
 SEED = 10547 + 3
 
 
+def save_arg(args):
+    """GlobalFit's save_products for --save."""
+    return {"auto": "auto", "on": True, "off": False}[getattr(args, "save", "auto")]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,6 +54,9 @@ def parse():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3", "tf32", "fp64tc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--save", choices=("auto", "on", "off"), default="auto",
+                    help="fit case: keep the forward's tensor-core products for the adjoint (GlobalFit's "
+                         "save_products: auto = where the table's ratio of table to product bytes pays)")
     ap.add_argument("--inner", type=int, default=10,
                     help="fit case: fit steps per bench step (the timed region is steps x inner fit steps)")
     ap.add_argument("--no-extras", action="store_true",
@@ -1187,7 +1195,8 @@ def run_descent(args):
     t0[..., 0] = np.log(g.params.A)[None, :] + rng.uniform(-0.3, 0.3, (REPLICAS, 14))
     t0[..., 1] = g.params.alpha[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
     t0[..., 2] = g.params.beta[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
-    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None)
+    fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
+                    save_products=save_arg(args))
     fit.capture()
     gd = PDFDescent(fit, t0, g.x, lr=0.02)
     for _ in range(max(3, args.warmup)):
@@ -1261,7 +1270,7 @@ def main():
     cov = W.covariance(o_true, SEED)
     D = np.concatenate(W.pseudo_data(o_true, SEED))
     fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
-                    pipelined=not args.phases, waves=args.waves)
+                    pipelined=not args.phases, waves=args.waves, save_products=save_arg(args))
     fit.capture()
     launches = fit.launches_per_step()
     stream = torch.cuda.current_stream()
@@ -1335,7 +1344,11 @@ def main():
             "data": "synthetic",
             "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
                            schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves",
-                           fit_steps_per_step=inner, ms_per_fit_step=fit_ms),
+                           fit_steps_per_step=inner, ms_per_fit_step=fit_ms,
+                           saved_products=f"{sum(b is not None for b in fit.saved)} of "
+                                          f"{sum(k == 'had' for k in fit.kinds)} hadronic tables, "
+                                          f"{sum(b.numel() * 4 for b in fit.saved if b is not None) / 1e6:.0f} MB "
+                                          f"(--save {args.save})"),
             "roofline": roof,
             "e2e": {"value": job_throughput(units, world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": inner * F_host.numel() * F_host.element_size(),

@@ -308,6 +308,45 @@ int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo,
                      void *gF, int accumulate, int prec, fk_stream stream);
 
 /*
+ * Saved forward products, for a fit step that runs the forward and then the
+ * adjoint of the same replicas (Sec. 2: each step of the gradient descent
+ * evaluates the observables, the chi^2 and its gradient).  With the channels
+ * of a hadronic table grouped by their first flavour a_g, the tensor-core
+ * forward forms, per group g, data point d and x point i,
+ *   Y_g[r][d][i] = sum_{c in g, j} FK[d][c][i][j] f^r_{b_c}(x_j)
+ * and reduces it with f^r_{a_g}(x_i) into O (Eq. 1).  The adjoint's
+ * derivative with respect to f^r_{a_g}(x_i) is sum_d gO[r][d] Y_g[r][d][i]:
+ * the same products, contracted with gO instead.  fk_had_conv_save keeps
+ * them, and fk_conv_backward_saved forms that term from them instead of a
+ * second tensor-core pass over the table; the other term (derivative with
+ * respect to the second flavour) is computed as in fk_conv_backward.
+ * Hadronic tables in the factorised form (not FK_TABLE_LUMI) and the modes
+ * FK_BF16, FK_BF16X3, FK_TF32 only.
+ *
+ * fk_saved_size: *bytes = the size of the buffer the two calls need for
+ * table t, R replicas and prec (4 * ceil(ndata / G) * groups * G * nx *
+ * ceil(R / 128) * 128, G the table's data points per tile; about
+ * 4 * ndata * groups * nx * R).  *bytes = 0 on error.
+ * fk_had_conv_save: fk_had_conv (same arguments, O bit for bit the same) that
+ * also writes the products to saved (DEVICE, 4-byte aligned, saved_bytes at
+ * least fk_saved_size; the layout is the library's own).
+ * fk_conv_backward_saved: fk_conv_backward (same arguments, gF bit for bit
+ * the same) for a saved buffer written by fk_had_conv_save with the same
+ * table, F, R and prec, ordered before this call (same stream or an event).
+ * Nothing checks that: products of another F give that F's first term.
+ * Errors: FK_EINVAL (as fk_had_conv / fk_conv_backward, NULL or misaligned
+ * saved, saved_bytes too small: the message gives the size needed),
+ * FK_EUNSUPPORTED (another mode, a mode not stored, a dense-form table),
+ * FK_ENOMEM, FK_ECUDA.
+ */
+int fk_saved_size(const fk_table *t, int R, int prec, size_t *bytes);
+int fk_had_conv_save(const fk_table *t, const void *F, int R, void *O, int ldo, void *saved,
+                     size_t saved_bytes, int prec, fk_stream stream);
+int fk_conv_backward_saved(const fk_table *t, const void *F, const void *gO, int ldgo, int R,
+                           const void *saved, size_t saved_bytes, void *gF, int accumulate, int prec,
+                           fk_stream stream);
+
+/*
  * Sum of gradient buffers, for adjoints computed concurrently (on several
  * streams, each into its own buffer) that must be combined in a fixed order:
  *   out[e] (+)= parts[0][e] + parts[1][e] + ... + parts[nparts-1][e]

@@ -21,8 +21,8 @@ import torch
 from . import _lib
 from ._lib import FKError, PRECS
 
-__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "dense_conv", "luminosity", "Cov", "chi2",
-           "FKConv", "Server", "FKError", "PRECS", "lib_path"]
+__all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "saved_size", "saved_buffer", "dense_conv",
+           "luminosity", "Cov", "chi2", "FKConv", "Server", "FKError", "PRECS", "lib_path"]
 
 NFL = 14
 
@@ -157,19 +157,44 @@ def _check_f(t, F, prec):
         raise ValueError(f"F must be a contiguous cuda {dt} tensor [R][14][{t.nxg}]")
 
 
-def conv(t: Table, F: torch.Tensor, prec="fp32", out: torch.Tensor = None) -> torch.Tensor:
+def conv(t: Table, F: torch.Tensor, prec="fp32", out: torch.Tensor = None,
+         save: torch.Tensor = None) -> torch.Tensor:
     """Observables O [R][ndata] of table t for replicas F [R][14][nx_grid].
 
     out may be a column slice out[:, off:off+ndata] of a wider [R][n] tensor
-    (unit stride along data points): the row stride is passed as ldo."""
+    (unit stride along data points): the row stride is passed as ldo.
+    save (hadronic tables, tensor-core modes): a buffer from saved_buffer
+    that receives the forward's products for conv_backward(..., saved=save)."""
     _check_f(t, F, prec)
     R = F.shape[0]
     O = out if out is not None else torch.empty((R, t.ndata), dtype=F.dtype, device=F.device)
     if O.shape != (R, t.ndata) or O.stride(1) != 1 or O.dtype != F.dtype:
         raise ValueError("out must be [R][ndata] with unit column stride and F's dtype")
+    if save is not None:
+        _lib.call("fk_had_conv_save", t.handle, _p(F), R, _p(O), O.stride(0), _p(save), _nbytes(save),
+                  _prec(prec), _stream())
+        return O
     name = "fk_had_conv" if t.kind == 1 else "fk_dis_conv"
     _lib.call(name, t.handle, _p(F), R, _p(O), O.stride(0), _prec(prec), _stream())
     return O
+
+
+def saved_size(t: Table, R: int, prec) -> int:
+    """Bytes of the saved-product buffer of table t for R replicas (fk_saved_size)."""
+    n = ctypes.c_size_t()
+    _lib.call("fk_saved_size", t.handle, int(R), _prec(prec), ctypes.byref(n))
+    return int(n.value)
+
+
+def saved_buffer(t: Table, R: int, prec, device="cuda") -> torch.Tensor:
+    """A device buffer for the forward's saved products (see conv's save)."""
+    return torch.empty(saved_size(t, R, prec) // 4, dtype=torch.float32, device=device)
+
+
+def _nbytes(x: torch.Tensor) -> int:
+    if not (x.is_cuda and x.is_contiguous()):
+        raise ValueError("the saved buffer must be a contiguous cuda tensor")
+    return x.numel() * x.element_size()
 
 
 def dis_conv(t, F, prec="fp32", out=None):
@@ -213,8 +238,11 @@ def luminosity(t: Table, F: torch.Tensor, prec="fp32", out: torch.Tensor = None)
     return L
 
 
-def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False):
-    """gF [R][14][nx_grid] (+)= sum_d gO[r][d] dO[r][d]/dF[r]."""
+def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False, saved=None):
+    """gF [R][14][nx_grid] (+)= sum_d gO[r][d] dO[r][d]/dF[r].
+
+    saved: the buffer a conv(..., save=saved) of the same F wrote before
+    (stream-ordered); the first-flavour term is then formed from it."""
     dt = _io_dtype(prec)
     R = gO.shape[0]
     if gF is None:
@@ -222,6 +250,10 @@ def conv_backward(t: Table, F, gO, prec="fp32", gF=None, accumulate=False):
         accumulate = False
     if gO.stride(1) != 1:
         raise ValueError("gO needs unit stride along data points")
+    if saved is not None:
+        _lib.call("fk_conv_backward_saved", t.handle, _p(F), _p(gO), gO.stride(0), R, _p(saved),
+                  _nbytes(saved), _p(gF), int(bool(accumulate)), _prec(prec), _stream())
+        return gF
     _lib.call("fk_conv_backward", t.handle, _p(F), _p(gO), gO.stride(0), R, _p(gF),
               int(bool(accumulate)), _prec(prec), _stream())
     return gF

@@ -30,6 +30,9 @@ SIGNATURES = {
     "fk_dense_conv": [P, P, I, P, I, I, P],
     "fk_luminosity": [P, P, I, P, I, P],
     "fk_conv_backward": [P, P, P, I, I, P, I, I, P],
+    "fk_saved_size": [P, I, I, ctypes.POINTER(SZ)],
+    "fk_had_conv_save": [P, P, I, P, I, P, SZ, I, P],
+    "fk_conv_backward_saved": [P, P, P, I, I, P, SZ, P, I, I, P],
     "fk_grad_sum": [P, I, ctypes.c_longlong, P, I, I, P],
     "fk_cov_create": [P, P, I, PP],
     "fk_cov_destroy": [P],

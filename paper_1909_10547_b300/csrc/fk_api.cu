@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <set>
 #include <utility>
@@ -228,6 +230,30 @@ int check_conv(const fk_table *t, int kind, const void *F, int R, const void *O,
     return FK_OK;
 }
 
+// The saved-product calls: a hadronic table in the factorised form, a
+// tensor-core mode it stores, and (when given) a buffer of at least
+// saved_elems floats, 4-byte aligned.
+int check_saved(const fk_table *t, int R, int prec, const void *saved, size_t saved_bytes, bool need_buf) {
+    if (!t) return fail(FK_EINVAL, "table is NULL");
+    if (t->kind != FK_KIND_HAD) return fail(FK_EINVAL, "saved products need a hadronic table");
+    if (R < 1) return fail(FK_EINVAL, "R < 1");
+    if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "unknown precision");
+    if (prec != FK_BF16 && prec != FK_BF16X3 && prec != FK_TF32)
+        return fail(FK_EUNSUPPORTED, "saved products only in the tensor-core modes BF16, BF16 hi+lo and TF32");
+    if (!(t->mask & FK_PREC_BIT(prec))) return fail(FK_EUNSUPPORTED, "precision not stored in this table");
+    if (t->tc.lum_on) return fail(FK_EUNSUPPORTED, "saved products need the factorised form");
+    if (!need_buf) return FK_OK;
+    if (!saved) return fail(FK_EINVAL, "null saved buffer");
+    if ((uintptr_t)saved % 4) return fail(FK_EINVAL, "saved buffer not 4-byte aligned");
+    const size_t need = saved_elems(t, R) * sizeof(float);
+    if (saved_bytes < need) {
+        char msg[96];
+        snprintf(msg, sizeof msg, "saved buffer too small: %zu bytes, %zu needed", saved_bytes, need);
+        return fail(FK_EINVAL, msg);
+    }
+    return FK_OK;
+}
+
 #ifdef FK_DEBUG
 // Writes buf[idx] through a debug check: with idx out of range the check
 // records it and the write is skipped.  Launched only in debug builds.
@@ -389,6 +415,35 @@ int fk_luminosity(const fk_table *t, const void *F, int R, void *L, int prec, fk
     if (R < 1) return fail(FK_EINVAL, "R < 1");
     if (prec < FK_FP64 || prec > FK_FP64_TC) return fail(FK_EINVAL, "unknown precision");
     return luminosity_cc(t, F, R, L, FK_IO64(prec), (cudaStream_t)stream);
+}
+
+int fk_saved_size(const fk_table *t, int R, int prec, size_t *bytes) {
+    if (!bytes) return fail(FK_EINVAL, "null bytes");
+    *bytes = 0;
+    const int rc = check_saved(t, R, prec, nullptr, 0, false);
+    if (rc) return rc;
+    *bytes = saved_elems(t, R) * sizeof(float);
+    return FK_OK;
+}
+
+int fk_had_conv_save(const fk_table *t, const void *F, int R, void *O, int ldo, void *saved, size_t saved_bytes,
+                     int prec, fk_stream stream) {
+    int rc = check_conv(t, FK_KIND_HAD, F, R, O, ldo, prec);
+    if (!rc) rc = check_saved(t, R, prec, saved, saved_bytes, true);
+    if (rc) return rc;
+    ldo = ldo ? ldo : t->ndata;
+    return fwd_tc_save(t, (const float *)F, R, (float *)O, ldo, (float *)saved, prec, (cudaStream_t)stream);
+}
+
+int fk_conv_backward_saved(const fk_table *t, const void *F, const void *gO, int ldgo, int R, const void *saved,
+                           size_t saved_bytes, void *gF, int accumulate, int prec, fk_stream stream) {
+    int rc = check_saved(t, R, prec, saved, saved_bytes, true);
+    if (rc) return rc;
+    if (!F || !gO || !gF) return fail(FK_EINVAL, "null F, gO or gF");
+    if (ldgo < 0 || (ldgo > 0 && ldgo < t->ndata)) return fail(FK_EINVAL, "ldgo < ndata");
+    ldgo = ldgo ? ldgo : t->ndata;
+    return bwd_tc_saved(t, (const float *)F, (const float *)gO, ldgo, R, (const float *)saved, (float *)gF,
+                        accumulate ? 1 : 0, prec, (cudaStream_t)stream);
 }
 
 int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo, int R, void *gF,

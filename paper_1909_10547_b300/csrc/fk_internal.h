@@ -232,6 +232,13 @@ int dis_bwd_tc(const fk_table *t, const float *gO, int ldgo, int R, float *gF, i
                cudaStream_t s);
 int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, float *gF,
            int accumulate, int prec, cudaStream_t s);
+// saved forward products (hadronic tables, factorised form): the forward also
+// writes its products Y_g (saved_elems floats), the adjoint forms its first
+// term from them
+size_t saved_elems(const fk_table *t, int R);
+int fwd_tc_save(const fk_table *t, const float *F, int R, float *O, int ldo, float *Y, int prec, cudaStream_t s);
+int bwd_tc_saved(const fk_table *t, const float *F, const float *gO, int ldgo, int R, const float *Y, float *gF,
+                 int accumulate, int prec, cudaStream_t s);
 void tc_free(fk_table *t);
 // operand-slice products (k_tc.cu) and FP64 on the tensor cores (k_oz.cu)
 int tc_map_bf16(CUtensorMap *m, const void *ptr, long long cols, long long rows, int box_rows);

@@ -334,6 +334,7 @@ struct TcParams {
     float *O;         // forward: observables, row stride ldo
     const float *gO;  // adjoint: weights gO[r * ldo + d]
     float *P;         // adjoint: partial sums [ntile_n][ngroups][nx][R_pad]
+    float *Y;         // forward, optional: the products Y_g saved as [ntile_n][ngroups][nrt][G * nx][128]
     // K split (dense products with fewer tiles than SMs): work item w covers
     // data tile nt and K split sp, ntile_n data tiles; split sp starts at K
     // element sp * kspl and writes its partial tile at O + sp * ostride
@@ -769,6 +770,15 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
                     if (MODE != MODE_DENSE && MODE != MODE_LUMI && c * 64 < ncols) {
                         uint32_t v[64];
                         tmem_ld64(taddr + (uint32_t)(c * 64), v);
+                        // forward with saved products: the raw columns, one
+                        // 128-byte line per warp and column, columns of a
+                        // replica tile 512 bytes apart (immediate offsets)
+                        if (MODE == MODE_FWD && p.Y && FK_DBG(nt < p.ntile_n && rt < p.nrt, 15, nt)) {
+                            float *y = p.Y + ((((size_t)nt * p.ngroups + g) * p.nrt + rt) * ncols + c * 64) * TC_M + rl;
+#pragma unroll
+                            for (int k = 0; k < 64; ++k)
+                                if (c * 64 + k < ncols) y[k * TC_M] = __uint_as_float(v[k]);
+                        }
 #pragma unroll
                         for (int k = 0; k < 64; ++k) {
                             const int col = c * 64 + k, i = col / G, dl = col % G;
@@ -1146,6 +1156,50 @@ __global__ void k_pack_lum(const double *__restrict__ fk, int ndata, int nc, int
     }
 }
 
+// Adjoint term 1 from the forward's saved products:
+//   P1[t][g][i][r] = sum_dl gO[r][t * G + dl] * Y[t][g][rt][i * G + dl][r % 128],
+// each sum a chain of fused multiply-adds over dl = 0 .. G-1 starting from 0,
+// the order in which the adjoint epilogue forms it from the accumulator, so
+// P1 is the one the tensor-core pass over the forward packing would write.
+// Grid (R_pad / 128, ngroups, ntile): replicas across threads (coalesced
+// loads of Y and stores of P1), the tile's G weights in registers, the loads
+// of UI x points in flight together.
+template <int G>
+__global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, const float *__restrict__ gO,
+                                                   int ldgo, int ndata, int nx, int ngroups, int R, int R_pad,
+                                                   float *__restrict__ P1) {
+    constexpr int UI = G <= 8 ? 4 : 2;
+    const int rt = blockIdx.x, r = rt * TC_M + threadIdx.x;
+    const int g = blockIdx.y, t = blockIdx.z;
+    float w[G];
+#pragma unroll
+    for (int dl = 0; dl < G; ++dl) {
+        const int dd = t * G + dl;
+        w[dl] = (r < R && dd < ndata) ? __ldg(gO + (size_t)r * ldgo + dd) : 0.f;
+    }
+    const size_t tg = (size_t)t * ngroups + g;
+    const float *y = Y + ((tg * gridDim.x + rt) * G * nx) * TC_M + threadIdx.x;
+    float *o = P1 + tg * nx * R_pad + r;
+    for (int i0 = 0; i0 < nx; i0 += UI) {
+        // x points past nx re-read the last one (every load unconditional,
+        // so all UI * G are issued before the first multiply-add)
+        float v[UI][G];
+#pragma unroll
+        for (int u = 0; u < UI; ++u) {
+            const float *yu = y + (size_t)min(i0 + u, nx - 1) * G * TC_M;
+#pragma unroll
+            for (int dl = 0; dl < G; ++dl) v[u][dl] = __ldg(yu + dl * TC_M);
+        }
+#pragma unroll
+        for (int u = 0; u < UI; ++u) {
+            float ps = 0.f;
+#pragma unroll
+            for (int dl = 0; dl < G; ++dl) ps = fmaf(w[dl], v[u][dl], ps);
+            if (i0 + u < nx) o[(size_t)(i0 + u) * R_pad] = ps;
+        }
+    }
+}
+
 // Adjoint gather: gF[r][a][m] (+)= sum_t P1[t][g1(a)][i(m)][r] + sum_t P2[t][g2(a)][i(m)][r]
 // with i(m) the table's x index of grid point m, g1/g2 the groups of flavour a
 // in the forward and transposed packings (-1: none).  Grid (ceil(R / 128),
@@ -1498,8 +1552,10 @@ __global__ void __launch_bounds__(256) k_dense_sum(const float *__restrict__ par
 template <int PREC>
 int lum_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s);
 
+// Y (optional): the products Y_g are also written there, as
+// [ntile_n][ngroups][G * nx][R_pad] floats (saved_elems)
 template <int PREC>
-int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
+int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s, float *Y = nullptr) {
     const TcLayout &L = t->tc;
     if (L.lum_on) return lum_tc_t<PREC>(t, F, R, O, ldo, s);
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
@@ -1513,6 +1569,7 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     p.ldo = ldo;
     p.Fm = Fm;
     p.O = O;
+    p.Y = Y;
     return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, L.fwd, p, s);
 }
 
@@ -1669,6 +1726,50 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
         const int rc = launch_tc_g<PREC, MODE_ADJ>(t, mA[k], mA2[k], *packs[k], p[k], s);
         if (rc) return rc;
     }
+    k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(
+        P1, P2, L.ntile_n, L.fwd.grp.ngroups, L.bwd.grp.ngroups, L.gmap, L.gmap + NFL, t->d_xinv, t->nx,
+        t->nxg, R, R_pad, accumulate, gF);
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
+
+// Adjoint with the forward's saved products Y: term 1 is contracted from Y
+// (k_adj_saved, the partial sums the forward-packing pass would write), term 2
+// is the tensor-core pass over the transposed packing as above, then the same
+// gather.
+template <int PREC>
+int bwd_tc_saved_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R, const float *Y,
+                   float *gF, int accumulate, cudaStream_t s) {
+    const TcLayout &L = t->tc;
+    const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
+    Scratch scr(s);
+    float *P1 = nullptr, *P2 = nullptr;
+    FK_CUDA(scr.get(&P1, (size_t)L.ntile_n * L.fwd.grp.ngroups * t->nx * R_pad));
+    FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
+    const dim3 grid((unsigned)(R_pad / TC_M), (unsigned)L.fwd.grp.ngroups, (unsigned)L.ntile_n);
+    const int ng = L.fwd.grp.ngroups, nd = t->ndata, nx = t->nx;
+    switch (L.G) {
+        case 4: k_adj_saved<4><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 5: k_adj_saved<5><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 6: k_adj_saved<6><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 7: k_adj_saved<7><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 8: k_adj_saved<8><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 12: k_adj_saved<12><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        case 16: k_adj_saved<16><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;
+        default: return fail(FK_EINVAL, "unexpected data points per tile");
+    }
+    count_launch();
+    FK_CUDA(cudaGetLastError());
+    CUtensorMap mA, mA2;
+    TcParams p;
+    int rc = prepare<PREC>(t, L.bwd, F, R, scr, nullptr, s, mA, mA2, p);
+    if (rc) return rc;
+    p.ldo = ldgo;
+    p.gO = gO;
+    p.P = P2;
+    rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, L.bwd, p, s);
+    if (rc) return rc;
     k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(
         P1, P2, L.ntile_n, L.fwd.grp.ngroups, L.bwd.grp.ngroups, L.gmap, L.gmap + NFL, t->d_xinv, t->nx,
         t->nxg, R, R_pad, accumulate, gF);
@@ -2104,6 +2205,31 @@ int bwd_tc(const fk_table *t, const float *F, const float *gO, int ldgo, int R, 
         case FK_BF16: return bwd_tc_t<FK_BF16>(t, F, gO, ldgo, R, gF, accumulate, s);
         case FK_BF16X3: return bwd_tc_t<FK_BF16X3>(t, F, gO, ldgo, R, gF, accumulate, s);
         case FK_TF32: return bwd_tc_t<FK_TF32>(t, F, gO, ldgo, R, gF, accumulate, s);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
+}
+
+size_t saved_elems(const fk_table *t, int R) {
+    const TcLayout &L = t->tc;
+    const size_t R_pad = (size_t)(R + TC_M - 1) / TC_M * TC_M;
+    return (size_t)L.ntile_n * L.fwd.grp.ngroups * L.G * t->nx * R_pad;
+}
+
+int fwd_tc_save(const fk_table *t, const float *F, int R, float *O, int ldo, float *Y, int prec, cudaStream_t s) {
+    switch (prec) {
+        case FK_BF16: return fwd_tc_t<FK_BF16>(t, F, R, O, ldo, s, Y);
+        case FK_BF16X3: return fwd_tc_t<FK_BF16X3>(t, F, R, O, ldo, s, Y);
+        case FK_TF32: return fwd_tc_t<FK_TF32>(t, F, R, O, ldo, s, Y);
+    }
+    return fail(FK_EINVAL, "not a tensor-core precision");
+}
+
+int bwd_tc_saved(const fk_table *t, const float *F, const float *gO, int ldgo, int R, const float *Y, float *gF,
+                 int accumulate, int prec, cudaStream_t s) {
+    switch (prec) {
+        case FK_BF16: return bwd_tc_saved_t<FK_BF16>(t, F, gO, ldgo, R, Y, gF, accumulate, s);
+        case FK_BF16X3: return bwd_tc_saved_t<FK_BF16X3>(t, F, gO, ldgo, R, Y, gF, accumulate, s);
+        case FK_TF32: return bwd_tc_saved_t<FK_TF32>(t, F, gO, ldgo, R, Y, gF, accumulate, s);
     }
     return fail(FK_EINVAL, "not a tensor-core precision");
 }

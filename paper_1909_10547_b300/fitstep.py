@@ -24,18 +24,30 @@ blocks, all adjoints), each its own graph, for per-phase timing.
 
 Either way the result does not depend on how the streams interleave: every
 table writes its own outputs and every sum runs in a fixed order.
+
+save_products (hadronic tables in the tensor-core modes): the forward also
+keeps its tensor-core products (fk_had_conv_save) and the adjoint forms its
+first-flavour term from them (fk_conv_backward_saved) instead of a second
+pass over the table; the results are bit for bit those of the plain calls.
+Saving writes 4 * ndata * groups * nx * R_pad bytes, where a pass over a
+BF16 hi+lo table reads 4 * ndata * nc * nx^2, so it pays where
+rho = nc * nx / (groups * R_pad) is large: measured alone (R = 100, BF16
+hi+lo) the ten largest tables of the global set gained 29-62 us per step
+from saving at rho >= 1.7, about nothing at rho = 1.1-1.4 and lost at
+rho < 1.  "auto" (default) saves where rho >= 1.25; True everywhere; False
+nowhere.
 """
 import numpy as np
 import torch
 
-from . import Cov, Table, _lib, chi2, conv, conv_backward, grad_sum
+from . import Cov, Table, _lib, chi2, conv, conv_backward, grad_sum, saved_buffer
 
 NFL = 14
 
 
 class GlobalFit:
     def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda",
-                 nstreams=None, pipelined=True, waves=1):
+                 nstreams=None, pipelined=True, waves=1, save_products="auto"):
         """tables: workloads.DisTable/HadTable list sharing one x grid;
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
@@ -48,6 +60,16 @@ class GlobalFit:
         # every table runs in the step's mode: in the reduced modes the DIS
         # tables are plain products on the tensor cores, like the hadronic ones
         self.tprec = [prec for _ in tables]
+        # per table: the buffer of its saved forward products, or None
+        tc = prec in ("bf16", "bf16x3", "tf32")
+        R_pad = -(-F.shape[0] // 128) * 128
+        self.saved = []
+        for t, tab, kind in zip(tables, self.tabs, self.kinds):
+            use = tc and kind == "had" and not tab.lumi and save_products is not False
+            if use and save_products == "auto":
+                groups = len(set(np.asarray(t.ca).tolist()))
+                use = t.nc * t.nx >= 1.25 * groups * R_pad
+            self.saved.append(saved_buffer(tab, F.shape[0], prec, device) if use else None)
         nd = [t.ndata for t in tables]
         self.offs = np.concatenate([[0], np.cumsum(nd)]).astype(int)
         self.ntot = int(self.offs[-1])
@@ -153,7 +175,8 @@ class GlobalFit:
     def forward(self):
         def body(s):
             for k in self.groups[s]:
-                conv(self.tabs[k], self.F, self.tprec[k], out=self.O[:, self.offs[k]:self.offs[k + 1]])
+                conv(self.tabs[k], self.F, self.tprec[k], out=self.O[:, self.offs[k]:self.offs[k + 1]],
+                     save=self.saved[k])
         self._fan_out(body)
 
     def loss(self):
@@ -163,7 +186,7 @@ class GlobalFit:
         def body(s):
             for n, k in enumerate(self.groups[s]):
                 conv_backward(self.tabs[k], self.F, self.gO[:, self.offs[k]:self.offs[k + 1]],
-                              self.tprec[k], gF=self.gF_parts[s], accumulate=n > 0)
+                              self.tprec[k], gF=self.gF_parts[s], accumulate=n > 0, saved=self.saved[k])
         self._fan_out(body)
         grad_sum([self.gF_parts[s] for s in range(self.nstreams) if self.groups[s]], self.gF)
 
@@ -212,7 +235,7 @@ class GlobalFit:
         """forward -> chi^2 -> adjoint of table k on the current stream;
         returns an event recorded after the forward."""
         cur = torch.cuda.current_stream()
-        conv(self.tabs[k], self.F, self.tprec[k], out=self.Ok[k])
+        conv(self.tabs[k], self.F, self.tprec[k], out=self.Ok[k], save=self.saved[k])
         fwd = torch.cuda.Event()
         fwd.record(cur)
         h = self.chi2_streams[k]
@@ -223,7 +246,7 @@ class GlobalFit:
             done.record(h)
         cur.wait_event(done)
         conv_backward(self.tabs[k], self.F, self.gOk[k], self.tprec[k], gF=self.gF_parts[s],
-                      accumulate=accumulate)
+                      accumulate=accumulate, saved=self.saved[k])
         return fwd
 
     def phases(self):

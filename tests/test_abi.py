@@ -136,3 +136,15 @@ def test_probe_argument_errors_need_no_gpu():
     assert lib.fk_mma_probe(64, 10, 2, ctypes.c_void_p(1), None) == _lib.FK_EINVAL    # fill not 0 or 1
     assert lib.fk_mma_probe(64, 10, 0, None, None) == _lib.FK_EINVAL                  # no output
     assert lib.fk_fma_probe(_lib.FK_BF16, 1, 1, ctypes.c_void_p(1), None) == _lib.FK_EINVAL
+
+
+def test_saved_product_argument_errors_need_no_gpu():
+    lib = _lib.load()
+    n = ctypes.c_size_t(7)
+    assert lib.fk_saved_size(None, 1, _lib.FK_BF16X3, ctypes.byref(n)) == _lib.FK_EINVAL  # no table
+    assert n.value == 0
+    assert lib.fk_saved_size(None, 1, _lib.FK_BF16X3, None) == _lib.FK_EINVAL            # no output
+    p = ctypes.c_void_p(16)
+    assert lib.fk_had_conv_save(None, p, 1, p, 0, p, 1 << 20, _lib.FK_BF16X3, None) == _lib.FK_EINVAL
+    assert lib.fk_conv_backward_saved(None, p, p, 0, 1, p, 1 << 20, p, 0, _lib.FK_BF16X3,
+                                      None) == _lib.FK_EINVAL

@@ -43,6 +43,13 @@ for (nd, nc, nx, R) in [(1, 1, 1, 1), (129, 1, 17, 3), (1, 5, 33, 257), (129, 3,
             g = fk.conv_backward(tab, Fd, torch.tensor(gO, dtype=dt, device="cuda"), prec).double().cpu().numpy()
             assert np.all(np.isfinite(g))
             worst = max(worst, err)
+            if prec in ("bf16", "bf16x3", "tf32") and hasattr(t, "ca"):
+                # saved forward products: the same O and gF bit for bit
+                sv = fk.saved_buffer(tab, R, prec)
+                O2 = fk.conv(tab, Fd, prec, save=sv).double().cpu().numpy()
+                g2 = fk.conv_backward(tab, Fd, torch.tensor(gO, dtype=dt, device="cuda"), prec,
+                                      saved=sv).double().cpu().numpy()
+                assert np.array_equal(O2, O) and np.array_equal(g2, g), (nd, nc, nx, R, prec)
 # the dense form of the hadronic forward (PDF matrix built in shared memory)
 for (nd, nc, nx, R) in [(1, 1, 1, 1), (129, 3, 17, 3), (300, 5, 33, 257)]:
     rng = np.random.default_rng(nd + nc + nx + R + 1)

@@ -167,3 +167,29 @@ def test_fit_step_reduced_precision_gradient(small_global, prec, tol):
     err = np.abs(fit.gF.double().cpu().numpy() - gF_ref).max() / np.abs(gF_ref).max()
     print(prec, "gradient rel err", err)
     assert err <= tol
+
+
+@pytest.mark.parametrize("pipelined", [True, False])
+def test_saved_products_do_not_change_the_step(small_global, pipelined):
+    """The step with the forward's saved products (the default in the
+    tensor-core modes) gives the chi^2 and gradient of the step without
+    them, bit for bit, eager and replayed from its graph."""
+    g, cov, D = small_global
+    res = []
+    for save in (False, True):
+        fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec="bf16x3", pipelined=pipelined,
+                        save_products=save)
+        assert any(b is not None for b in fit.saved) == save
+        fit.step()
+        torch.cuda.synchronize()
+        res.append((fit.chi2.cpu().numpy().copy(), fit.gF.cpu().numpy().copy()))
+        if save:
+            fit.capture()
+            fit.chi2.zero_()
+            fit.gF.zero_()
+            fit.step()
+            torch.cuda.synchronize()
+            res.append((fit.chi2.cpu().numpy().copy(), fit.gF.cpu().numpy().copy()))
+    for chi, gF in res[1:]:
+        assert np.array_equal(chi, res[0][0])
+        assert np.array_equal(gF, res[0][1])

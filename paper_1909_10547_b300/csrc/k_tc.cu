@@ -1161,16 +1161,19 @@ __global__ void k_pack_lum(const double *__restrict__ fk, int ndata, int nc, int
 // each sum a chain of fused multiply-adds over dl = 0 .. G-1 starting from 0,
 // the order in which the adjoint epilogue forms it from the accumulator, so
 // P1 is the one the tensor-core pass over the forward packing would write.
-// Grid (R_pad / 128, ngroups, ntile): replicas across threads (coalesced
-// loads of Y and stores of P1), the tile's G weights in registers, the loads
-// of UI x points in flight together.
+// Grid (R_pad / 128 * ADJ_XS, ngroups, ntile): replicas across threads
+// (coalesced loads of Y and stores of P1), the x points split over ADJ_XS
+// blocks, the tile's G weights in registers, the loads of UI x points in
+// flight together.
+constexpr int ADJ_XS = 2;
 template <int G>
 __global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, const float *__restrict__ gO,
                                                    int ldgo, int ndata, int nx, int ngroups, int R, int R_pad,
                                                    float *__restrict__ P1) {
     constexpr int UI = G <= 8 ? 4 : 2;
-    const int rt = blockIdx.x, r = rt * TC_M + threadIdx.x;
+    const int rt = blockIdx.x / ADJ_XS, xs = blockIdx.x % ADJ_XS, r = rt * TC_M + threadIdx.x;
     const int g = blockIdx.y, t = blockIdx.z;
+    const int ibeg = xs * nx / ADJ_XS, iend = (xs + 1) * nx / ADJ_XS;
     float w[G];
 #pragma unroll
     for (int dl = 0; dl < G; ++dl) {
@@ -1178,15 +1181,15 @@ __global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, 
         w[dl] = (r < R && dd < ndata) ? __ldg(gO + (size_t)r * ldgo + dd) : 0.f;
     }
     const size_t tg = (size_t)t * ngroups + g;
-    const float *y = Y + ((tg * gridDim.x + rt) * G * nx) * TC_M + threadIdx.x;
+    const float *y = Y + ((tg * (gridDim.x / ADJ_XS) + rt) * G * nx) * TC_M + threadIdx.x;
     float *o = P1 + tg * nx * R_pad + r;
-    for (int i0 = 0; i0 < nx; i0 += UI) {
-        // x points past nx re-read the last one (every load unconditional,
-        // so all UI * G are issued before the first multiply-add)
+    for (int i0 = ibeg; i0 < iend; i0 += UI) {
+        // x points past the block's range re-read its last one (every load
+        // unconditional, so all UI * G are issued before the first multiply-add)
         float v[UI][G];
 #pragma unroll
         for (int u = 0; u < UI; ++u) {
-            const float *yu = y + (size_t)min(i0 + u, nx - 1) * G * TC_M;
+            const float *yu = y + (size_t)min(i0 + u, iend - 1) * G * TC_M;
 #pragma unroll
             for (int dl = 0; dl < G; ++dl) v[u][dl] = __ldg(yu + dl * TC_M);
         }
@@ -1195,7 +1198,7 @@ __global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, 
             float ps = 0.f;
 #pragma unroll
             for (int dl = 0; dl < G; ++dl) ps = fmaf(w[dl], v[u][dl], ps);
-            if (i0 + u < nx) o[(size_t)(i0 + u) * R_pad] = ps;
+            if (i0 + u < iend) o[(size_t)(i0 + u) * R_pad] = ps;
         }
     }
 }
@@ -1747,7 +1750,7 @@ int bwd_tc_saved_t(const fk_table *t, const float *F, const float *gO, int ldgo,
     float *P1 = nullptr, *P2 = nullptr;
     FK_CUDA(scr.get(&P1, (size_t)L.ntile_n * L.fwd.grp.ngroups * t->nx * R_pad));
     FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
-    const dim3 grid((unsigned)(R_pad / TC_M), (unsigned)L.fwd.grp.ngroups, (unsigned)L.ntile_n);
+    const dim3 grid((unsigned)(R_pad / TC_M * ADJ_XS), (unsigned)L.fwd.grp.ngroups, (unsigned)L.ntile_n);
     const int ng = L.fwd.grp.ngroups, nd = t->ndata, nx = t->nx;
     switch (L.G) {
         case 4: k_adj_saved<4><<<grid, 128, 0, s>>>(Y, gO, ldgo, nd, nx, ng, R, R_pad, P1); break;

@@ -34,8 +34,8 @@ BF16 hi+lo table reads 4 * ndata * nc * nx^2, so it pays where
 rho = nc * nx / (groups * R_pad) is large: measured alone (R = 100, BF16
 hi+lo) the ten largest tables of the global set gained 29-62 us per step
 from saving at rho >= 1.7, about nothing at rho = 1.1-1.4 and lost at
-rho < 1.  "auto" (default) saves where rho >= 1.25; True everywhere; False
-nowhere.
+rho < 1.  "auto" (default) saves where rho >= save_ratio (1.25); True
+everywhere; False nowhere.
 """
 import numpy as np
 import torch
@@ -47,7 +47,7 @@ NFL = 14
 
 class GlobalFit:
     def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda",
-                 nstreams=None, pipelined=True, waves=1, save_products="auto"):
+                 nstreams=None, pipelined=True, waves=1, save_products="auto", save_ratio=1.25):
         """tables: workloads.DisTable/HadTable list sharing one x grid;
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
@@ -68,7 +68,7 @@ class GlobalFit:
             use = tc and kind == "had" and not tab.lumi and save_products is not False
             if use and save_products == "auto":
                 groups = len(set(np.asarray(t.ca).tolist()))
-                use = t.nc * t.nx >= 1.25 * groups * R_pad
+                use = t.nc * t.nx >= save_ratio * groups * R_pad
             self.saved.append(saved_buffer(tab, F.shape[0], prec, device) if use else None)
         nd = [t.ndata for t in tables]
         self.offs = np.concatenate([[0], np.cumsum(nd)]).astype(int)

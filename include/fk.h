@@ -329,7 +329,8 @@ int fk_conv_backward(const fk_table *t, const void *F, const void *gO, int ldgo,
  * 4 * ndata * groups * nx * R).  *bytes = 0 on error.
  * fk_had_conv_save: fk_had_conv (same arguments, O bit for bit the same) that
  * also writes the products to saved (DEVICE, 4-byte aligned, saved_bytes at
- * least fk_saved_size; the layout is the library's own).
+ * least fk_saved_size; the layout is the library's own, and the part of it
+ * that belongs to padding replicas past R is left unwritten).
  * fk_conv_backward_saved: fk_conv_backward (same arguments, gF bit for bit
  * the same) for a saved buffer written by fk_had_conv_save with the same
  * table, F, R and prec, ordered before this call (same stream or an event).

@@ -772,8 +772,9 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
                         tmem_ld64(taddr + (uint32_t)(c * 64), v);
                         // forward with saved products: the raw columns, one
                         // 128-byte line per warp and column, columns of a
-                        // replica tile 512 bytes apart (immediate offsets)
-                        if (MODE == MODE_FWD && p.Y && FK_DBG(nt < p.ntile_n && rt < p.nrt, 15, nt)) {
+                        // replica tile 512 bytes apart (immediate offsets);
+                        // padding replicas (r >= R) store nothing
+                        if (MODE == MODE_FWD && p.Y && r < p.R && FK_DBG(nt < p.ntile_n && rt < p.nrt, 15, nt)) {
                             float *y = p.Y + ((((size_t)nt * p.ngroups + g) * p.nrt + rt) * ncols + c * 64) * TC_M + rl;
 #pragma unroll
                             for (int k = 0; k < 64; ++k)
@@ -1161,6 +1162,9 @@ __global__ void k_pack_lum(const double *__restrict__ fk, int ndata, int nc, int
 // each sum a chain of fused multiply-adds over dl = 0 .. G-1 starting from 0,
 // the order in which the adjoint epilogue forms it from the accumulator, so
 // P1 is the one the tensor-core pass over the forward packing would write.
+// The forward stores no products for padding replicas (r >= R): their
+// threads read replica R - 1's (written, finite) with weights 0, so their
+// partial sums are 0 as in that pass.
 // Grid (R_pad / 128 * ADJ_XS, ngroups, ntile): replicas across threads
 // (coalesced loads of Y and stores of P1), the x points split over ADJ_XS
 // blocks, the tile's G weights in registers, the loads of UI x points in
@@ -1181,7 +1185,8 @@ __global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, 
         w[dl] = (r < R && dd < ndata) ? __ldg(gO + (size_t)r * ldgo + dd) : 0.f;
     }
     const size_t tg = (size_t)t * ngroups + g;
-    const float *y = Y + ((tg * (gridDim.x / ADJ_XS) + rt) * G * nx) * TC_M + threadIdx.x;
+    const int lane_src = r < R ? (int)threadIdx.x : R - 1 - rt * TC_M;
+    const float *y = Y + ((tg * (gridDim.x / ADJ_XS) + rt) * G * nx) * TC_M + lane_src;
     float *o = P1 + tg * nx * R_pad + r;
     for (int i0 = ibeg; i0 < iend; i0 += UI) {
         // x points past the block's range re-read its last one (every load

@@ -42,7 +42,10 @@ def both(tab, F, gO, prec, ldo=0, accumulate=False, gF0=None):
     gOw[:, :tab.ndata] = torch.tensor(gO, dtype=torch.float32, device="cuda")
     gOd = gOw[:, :tab.ndata]
     out = []
-    for saved in (None, fk.saved_buffer(tab, R, prec)):
+    # NaN everywhere first: a product read that the forward did not write
+    # would reach gF
+    sv = fk.saved_buffer(tab, R, prec).fill_(float("nan"))
+    for saved in (None, sv):
         Ow = torch.full((R, wide), float("nan"), device="cuda")
         O = fk.conv(tab, Fd, prec, out=Ow[:, :tab.ndata], save=saved)
         gF = (gF0.clone() if gF0 is not None else torch.full((R, 14, tab.nxg), float("nan"), device="cuda"))

@@ -148,6 +148,10 @@ struct TcPack {
     // the same tensors with boxes of n_rows / 2 rows: each CTA of a pair
     // running 2-SM MMAs loads one half of every B tile
     CUtensorMap half_hi, half_lo, half_f32;
+    // hi+lo on single CTAs: boxes of 64-byte rows (64-byte swizzle); nar
+    // tells whether they were built
+    CUtensorMap nar_hi, nar_lo;
+    bool nar = false;
 };
 
 struct TcLayout {

@@ -176,12 +176,25 @@ __host__ __device__ constexpr uint64_t sw128_desc(uint32_t addr) {
            | (uint64_t)1 << 46                  // version
            | (uint64_t)2 << 61;                 // SWIZZLE_128B
 }
+// The same for rows of 64 B (64-byte swizzle, 8-row groups 512 B apart).
+__host__ __device__ constexpr uint64_t sw64_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4)  // start address, 16-byte units
+           | (uint64_t)1 << 16                  // LBO (unused for swizzled K-major)
+           | (uint64_t)(512 >> 4) << 32         // SBO
+           | (uint64_t)1 << 46                  // version
+           | (uint64_t)4 << 61;                 // SWIZZLE_64B
+}
 // The same descriptor in two words: desc_lo (start address and LBO) varies
 // per operand and K step, DESC_HI (SBO, version, swizzle) is shared.
 constexpr uint32_t DESC_HI = (uint32_t)(sw128_desc(0) >> 32);
+constexpr uint32_t DESC_HI64 = (uint32_t)(sw64_desc(0) >> 32);
 __host__ __device__ constexpr uint32_t desc_lo(uint32_t addr) { return (uint32_t)sw128_desc(addr); }
-__host__ __device__ constexpr uint64_t desc64(uint32_t lo) { return ((uint64_t)DESC_HI << 32) | lo; }
+template <bool NW = false>
+__host__ __device__ constexpr uint64_t desc64(uint32_t lo) {
+    return ((uint64_t)(NW ? DESC_HI64 : DESC_HI) << 32) | lo;
+}
 static_assert(desc64(desc_lo(0x2A7C0u)) == sw128_desc(0x2A7C0u), "descriptor split");
+static_assert(desc64<true>(desc_lo(0x2A7C0u)) == sw64_desc(0x2A7C0u), "descriptor split (64-byte rows)");
 static_assert(desc_lo(0x2A7C0u) + 0x403u == desc_lo(0x2A7C0u + 0x4030u), "a K-step offset adds to the address field");
 // D[tmem] (+)= A * B^T for one K step.  CG = 1: M = 128 rows of this CTA.
 // CG = 2 (issued by the even CTA of a pair): M = 256, rows 0..127 from the even
@@ -284,24 +297,28 @@ __device__ __forceinline__ float tf32_rna(float v) {
 }
 
 // ------------------------------------------------------------ kernel ----
-template <int PREC>
+// NW (narrow rows): 64-byte swizzled rows instead of 128-byte ones, so a
+// stage spans half the K and half the bytes and twice as many stages fit
+// (used for hi+lo on single CTAs, whose 96 KB stages otherwise allow only two).
+template <int PREC, bool NW = false>
 struct Tr {
     static constexpr bool X3 = PREC == FK_BF16X3;
     static constexpr int ESZ = PREC == FK_TF32 ? 4 : 2;
-    static constexpr int KC = 128 / ESZ;      // K elements per 128-byte swizzled row
-    static constexpr int KSTEP = 32 / ESZ;    // K per MMA instruction
-    static constexpr int NOPS = X3 ? 2 : 1;   // operand copies (hi, lo)
-    // 128-byte swizzle atoms per stage along K: two for the single-copy modes
-    // (8 MMAs between stage barriers), one for hi+lo (already 12 MMAs)
+    static constexpr int ROWB = NW ? 64 : 128;  // bytes per swizzled row
+    static constexpr int KC = ROWB / ESZ;       // K elements per swizzled row
+    static constexpr int KSTEP = 32 / ESZ;      // K per MMA instruction
+    static constexpr int NOPS = X3 ? 2 : 1;     // operand copies (hi, lo)
+    // swizzle atoms per stage along K: two for the single-copy modes (8 MMAs
+    // between stage barriers), one for hi+lo (already 12 MMAs, 6 with NW)
     static constexpr int ATOMS = X3 ? 1 : 2;
-    static constexpr int KCS = KC * ATOMS;    // K elements per stage
+    static constexpr int KCS = KC * ATOMS;      // K elements per stage
     static constexpr uint32_t FMT = PREC == FK_TF32 ? 2u : 1u;  // TF32 : BF16
 };
 // Pipeline depth: a CTA of a pair holds half of each B tile, so its stages
-// are smaller and more of them fit.
-template <int PREC, int CL>
+// are smaller and more of them fit; narrow rows halve a stage again.
+template <int PREC, int CL, bool NW = false>
 __host__ __device__ constexpr int tc_stages() {
-    return CL == 2 ? 3 : 2;
+    return NW ? 4 : CL == 2 ? 3 : 2;
 }
 
 // Epilogue modes of the tensor-core kernel.
@@ -335,6 +352,7 @@ struct TcParams {
     const float *gO;  // adjoint: weights gO[r * ldo + d]
     float *P;         // adjoint: partial sums [ntile_n][ngroups][nx][R_pad]
     float *Y;         // forward, optional: the products Y_g saved as [ntile_n][ngroups][nrt][G * nx][128]
+    int narrow;       // host side: the launch runs hi+lo single CTAs on 64-byte rows
     // K split (dense products with fewer tiles than SMs): work item w covers
     // data tile nt and K split sp, ntile_n data tiles; split sp starts at K
     // element sp * kspl and writes its partial tile at O + sp * ostride
@@ -363,10 +381,11 @@ struct TcParams {
 };
 
 
-template <int PREC, int CL>
+template <int PREC, int CL, bool NW = false>
 size_t tc_smem_bytes(int n_rows) {
-    const size_t stage = (size_t)Tr<PREC>::NOPS * Tr<PREC>::ATOMS * (TC_M * 128 + (size_t)(n_rows / CL) * 128);
-    return 1024 + tc_stages<PREC, CL>() * stage + 512;
+    using T = Tr<PREC, NW>;
+    const size_t stage = (size_t)T::NOPS * T::ATOMS * (TC_M * T::ROWB + (size_t)(n_rows / CL) * T::ROWB);
+    return 1024 + tc_stages<PREC, CL, NW>() * stage + 512;
 }
 
 // One work item is a (replica tile, data tile) pair of the product
@@ -378,13 +397,14 @@ size_t tc_smem_bytes(int n_rows) {
 //  the table tile.  The even CTA issues the MMAs; the copies of both CTAs
 //  complete on its `full` barriers, its commits release `empty` and signal
 //  `accf` in both CTAs, and both CTAs' epilogues release its `acce`.
-template <int PREC, int G, int MODE, int CL>
+template <int PREC, int G, int MODE, int CL, bool NW = false>
 __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
     k_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
          const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
          TcParams p) {
-    using T = Tr<PREC>;
-    constexpr int S = tc_stages<PREC, CL>();
+    static_assert(!NW || (CL == 1 && MODE != MODE_LUMI), "narrow rows: single CTAs, copied A operand");
+    using T = Tr<PREC, NW>;
+    constexpr int S = tc_stages<PREC, CL, NW>();
     const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
     const bool leader = rank == 0;
     // work items: tiles (CL = 1) or pairs of replica tiles (CL = 2)
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const int b_rows = p.n_rows / CL;  // B rows held by this CTA
-    const uint32_t a_bytes = TC_M * 128, b_bytes = (uint32_t)b_rows * 128;
+    const uint32_t a_bytes = TC_M * T::ROWB, b_bytes = (uint32_t)b_rows * T::ROWB;
     const uint32_t stage_bytes = T::NOPS * T::ATOMS * (a_bytes + b_bytes);
     // a stage: the A atoms, then the B atoms (then the lo copies for hi+lo)
     const uint32_t offB = T::ATOMS * a_bytes, offA2 = T::ATOMS * (a_bytes + b_bytes), offB2 = offA2 + offB;
@@ -588,7 +608,7 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
         // below 256 KB, so the 14-bit field never carries), and the
         // accumulator address changes only when a group ends.
         const uint32_t bstep = b_bytes >> 4;           // one B atom, descriptor units
-        constexpr uint32_t ASTEP = (TC_M * 128) >> 4;  // one A atom
+        constexpr uint32_t ASTEP = (TC_M * T::ROWB) >> 4;  // one A atom
         const int ng = p.ngroups;
         const int klast = sk[NFL + ng - 1];  // K after the last group
         int it = 0, gc = 0;
@@ -619,10 +639,10 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
                         const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 2u;
                         const uint32_t ao = atom * ASTEP + off, bo = atom * bstep + off;
-                        mma<PREC, CL>(d, desc64(a0 + ao), desc64(b0 + bo), idesc, k != kb);
+                        mma<PREC, CL>(d, desc64<NW>(a0 + ao), desc64<NW>(b0 + bo), idesc, k != kb);
                         if (T::X3) {
-                            mma<PREC, CL>(d, desc64(a0 + ao), desc64(b20 + bo), idesc, 1);
-                            mma<PREC, CL>(d, desc64(a20 + ao), desc64(b0 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64<NW>(a0 + ao), desc64<NW>(b20 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64<NW>(a20 + ao), desc64<NW>(b0 + bo), idesc, 1);
                         }
                         if (k + T::KSTEP == ke) {
                             if (CL == 2)
@@ -659,10 +679,10 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
                         const uint32_t atom = (uint32_t)(ks / (T::KC / T::KSTEP));
                         const uint32_t off = (uint32_t)(ks % (T::KC / T::KSTEP)) * 2u;
                         const uint32_t ao = atom * ASTEP + off, bo = atom * bstep + off;
-                        mma<PREC, CL>(d, desc64(a0 + ao), desc64(b0 + bo), idesc, k != kb);
+                        mma<PREC, CL>(d, desc64<NW>(a0 + ao), desc64<NW>(b0 + bo), idesc, k != kb);
                         if (T::X3) {
-                            mma<PREC, CL>(d, desc64(a0 + ao), desc64(b20 + bo), idesc, 1);
-                            mma<PREC, CL>(d, desc64(a20 + ao), desc64(b0 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64<NW>(a0 + ao), desc64<NW>(b20 + bo), idesc, 1);
+                            mma<PREC, CL>(d, desc64<NW>(a20 + ao), desc64<NW>(b0 + bo), idesc, 1);
                         }
                         if (k + T::KSTEP == ke) {
                             if (CL == 2)
@@ -1267,17 +1287,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 // 2-D K-major operand [rows][cols] with 128-byte swizzled boxes of
 // (128 B) x box_rows.
-int make_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_rows) {
+// rowb: bytes per box row and swizzle span, 128 (default) or 64
+int make_map(CUtensorMap *m, const void *ptr, int esz, long long cols, long long rows, int box_rows,
+             int rowb = 128) {
     auto fn = encoder();
     if (!fn) return fail(FK_ECUDA, "cuTensorMapEncodeTiled is not available");
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
-    const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                     const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    rowb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(FK_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return FK_OK;
 }
@@ -1355,12 +1377,24 @@ int max_clusters(K kernel, size_t smem, int threads) {
 // second operand copy) and half tiles for the CTA-pair launch.
 struct BMaps {
     const CUtensorMap *b, *b2, *h, *h2;
+    const CUtensorMap *n = nullptr, *n2 = nullptr;  // hi+lo, 64-byte rows (or NULL)
 };
 template <int PREC>
 BMaps b_maps(const TcPack &pk) {
     if (PREC == FK_TF32) return {&pk.map_f32, &pk.map_f32, &pk.half_f32, &pk.half_f32};
-    if (PREC == FK_BF16X3) return {&pk.map_hi, &pk.map_lo, &pk.half_hi, &pk.half_lo};
+    if (PREC == FK_BF16X3)
+        return {&pk.map_hi, &pk.map_lo, &pk.half_hi, &pk.half_lo, pk.nar ? &pk.nar_hi : nullptr,
+                pk.nar ? &pk.nar_lo : nullptr};
     return {&pk.map_hi, &pk.map_hi, &pk.half_hi, &pk.half_hi};
+}
+
+// The hi+lo B maps of 64-byte rows for a packing that stores both copies.
+int make_narrow_maps(TcPack &pk, long long rows) {
+    if (!pk.hi || !pk.lo) return FK_OK;
+    int rc = make_map(&pk.nar_hi, pk.hi, 2, pk.ktot_pad, rows, pk.n_rows, 64);
+    if (!rc) rc = make_map(&pk.nar_lo, pk.lo, 2, pk.ktot_pad, rows, pk.n_rows, 64);
+    pk.nar = rc == FK_OK;
+    return rc;
 }
 
 // Accumulator hand-off.  Use u of the NB-buffered accumulator (one use per
@@ -1392,19 +1426,23 @@ uint32_t tc_pwait(const TcParams &p, int S, int KCS) {
     return pwait;
 }
 
+// CTA pairs (256-row MMAs on two SMs) whenever the replica tiles pair up
+// and the channel groups span two stages or more on average.  A pair halves
+// the B bytes each SM loads but adds cross-SM hand-offs per stage and per
+// group; with groups of about one stage (config-2 shaped tables) single CTAs
+// measured faster (BF16 forward 30.8 against 34.9 us), with long groups or one
+// group pairs win (stress table BF16 1081 against 1030 TFLOP/s, the Table 3
+// product 381 against 416 us).  nchunks counts stages of 128-byte rows.
+bool use_pairs(const TcParams &p) {
+    const bool long_groups = p.ngroups == 1 || p.nchunks >= 2 * p.ngroups;
+    return p.nrt % 2 == 0 && long_groups;
+}
+
 template <int PREC, int G, int MODE>
 int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const BMaps &mb,
-              const TcParams &p0, cudaStream_t s) {
+              const TcParams &p0, cudaStream_t s, const CUtensorMap *nA = nullptr) {
     TcParams p = p0;
-    // CTA pairs (256-row MMAs on two SMs) whenever the replica tiles pair up
-    // and the channel groups span two stages or more on average.  A pair
-    // halves the B bytes each SM loads but adds cross-SM hand-offs per stage
-    // and per group; with groups of about one stage (config-2 shaped tables)
-    // single CTAs measured faster (BF16 forward 30.8 against 34.9 us), with
-    // long groups or one group pairs win (stress table BF16 1081 against 1030
-    // TFLOP/s, the Table 3 product 381 against 416 us).
-    const bool long_groups = p.ngroups == 1 || p.nchunks >= 2 * p.ngroups;
-    if (p.nrt % 2 == 0 && long_groups) {
+    if (!p.narrow && use_pairs(p)) {
         p.pwait = tc_pwait(p, tc_stages<PREC, 2>(), Tr<PREC>::KCS);
         auto kern = k_tc<PREC, G, MODE, 2>;
         const size_t smem = one_per_sm(tc_smem_bytes<PREC, 2>(p.n_rows));
@@ -1432,11 +1470,38 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
             return FK_OK;
         }
     }
+    const int grid = std::min(p.ntiles, sm_count());
+    if constexpr (PREC == FK_BF16X3 && MODE != MODE_LUMI) {
+        // hi+lo on single CTAs: 64-byte rows, four stages of half the K (the
+        // 96 KB stages of 128-byte rows leave room for two); the same MMAs in
+        // the same order, so the same results
+        if (p.narrow && nA && mb.n) {
+            constexpr int NK = Tr<PREC>::KCS / Tr<PREC, true>::KCS;  // narrow stages per wide one
+            p.nchunks *= NK;
+            p.spc *= NK;
+            p.pwait = tc_pwait(p, tc_stages<PREC, 1, true>(), Tr<PREC, true>::KCS);
+            auto kern = k_tc<PREC, G, MODE, 1, true>;
+            int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1, true>(256));
+            if (rc) return rc;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.gridDim = dim3(grid, 1, 1);
+            cfg.blockDim = dim3(tc_threads<MODE>(), 1, 1);
+            cfg.dynamicSmemBytes = one_per_sm(tc_smem_bytes<PREC, 1, true>(p.n_rows));
+            cfg.stream = s;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            FK_CUDA(cudaLaunchKernelEx(&cfg, kern, nA[0], nA[1], *mb.n, *mb.n2, p));
+            count_launch();
+            return FK_OK;
+        }
+    }
     p.pwait = tc_pwait(p, tc_stages<PREC, 1>(), Tr<PREC>::KCS);
     auto kern = k_tc<PREC, G, MODE, 1>;
     int rc = opt_in_smem(kern, tc_smem_bytes<PREC, 1>(256));
     if (rc) return rc;
-    const int grid = std::min(p.ntiles, sm_count());
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1454,16 +1519,16 @@ int launch_tc(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, 
 
 template <int PREC, int MODE>
 int launch_tc_g(const fk_table *t, const CUtensorMap &mA, const CUtensorMap &mA2, const TcPack &pk,
-                const TcParams &p, cudaStream_t s) {
+                const TcParams &p, cudaStream_t s, const CUtensorMap *nA = nullptr) {
     const BMaps mb = b_maps<PREC>(pk);
     switch (t->tc.G) {
-        case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mb, p, s);
-        case 5: return launch_tc<PREC, 5, MODE>(t, mA, mA2, mb, p, s);
-        case 6: return launch_tc<PREC, 6, MODE>(t, mA, mA2, mb, p, s);
-        case 7: return launch_tc<PREC, 7, MODE>(t, mA, mA2, mb, p, s);
-        case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mb, p, s);
-        case 12: return launch_tc<PREC, 12, MODE>(t, mA, mA2, mb, p, s);
-        case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mb, p, s);
+        case 4: return launch_tc<PREC, 4, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 5: return launch_tc<PREC, 5, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 6: return launch_tc<PREC, 6, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 7: return launch_tc<PREC, 7, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 8: return launch_tc<PREC, 8, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 12: return launch_tc<PREC, 12, MODE>(t, mA, mA2, mb, p, s, nA);
+        case 16: return launch_tc<PREC, 16, MODE>(t, mA, mA2, mb, p, s, nA);
     }
     return fail(FK_EINVAL, "bad tile height");
 }
@@ -1485,7 +1550,7 @@ cudaError_t launch_pack(const PackDst &d0, const PackDst &d1, const float *F, in
 template <int PREC>
 int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch &scr, float *Fm,
             cudaStream_t s, CUtensorMap &mA, CUtensorMap &mA2, TcParams &p, int frow_in = -1,
-            PackDst *defer = nullptr) {
+            PackDst *defer = nullptr, CUtensorMap *nar = nullptr) {
     const int R_pad = (R + TC_M - 1) / TC_M * TC_M;
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
     float *f32 = nullptr;
@@ -1516,11 +1581,6 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
             FK_CUDA(launch_pack<PREC>(d, PackDst{}, F, frow, R, R_pad, s));
         }
     }
-    const int esz = Tr<PREC>::ESZ;
-    int rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
-    if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);
-    if (rc) return rc;
-    if (PREC != FK_BF16X3) mA2 = mA;
     p = TcParams{};
     p.npair = 1;  // pa = pb = 0: one operand pair
     p.nrt = R_pad / TC_M;
@@ -1542,7 +1602,20 @@ int prepare(const fk_table *t, const TcPack &pk, const float *F, int R, Scratch 
         p.kbeg[g] = pk.grp.kbeg[g];
         p.kend[g] = pk.grp.kend[g];
     }
-    return FK_OK;
+    // the A maps of the launch shape: 64-byte rows (nar[0], nar[1]) for hi+lo
+    // on single CTAs when the packing has its narrow B maps, else 128-byte rows
+    const int esz = Tr<PREC>::ESZ;
+    p.narrow = PREC == FK_BF16X3 && nar && pk.nar && !use_pairs(p);
+    int rc;
+    if (p.narrow) {
+        rc = make_map(&nar[0], hi, esz, pk.ktot_pad, R_pad, TC_M, 64);
+        if (!rc) rc = make_map(&nar[1], lo, esz, pk.ktot_pad, R_pad, TC_M, 64);
+    } else {
+        rc = make_map(&mA, PREC == FK_TF32 ? (const void *)f32 : (const void *)hi, esz, pk.ktot_pad, R_pad, TC_M);
+        if (!rc && PREC == FK_BF16X3) rc = make_map(&mA2, lo, esz, pk.ktot_pad, R_pad, TC_M);
+        if (PREC != FK_BF16X3) mA2 = mA;
+    }
+    return rc;
 }
 
 // O[r][d] = sum over splits sp (in order) of part[sp][r][d]
@@ -1570,15 +1643,15 @@ int fwd_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaSt
     Scratch scr(s);
     float *Fm = nullptr;
     FK_CUDA(scr.get(&Fm, (size_t)L.fwd.grp.ngroups * t->nx * R_pad));
-    CUtensorMap mA, mA2;
+    CUtensorMap mA, mA2, nA[2];
     TcParams p;
-    int rc = prepare<PREC>(t, L.fwd, F, R, scr, Fm, s, mA, mA2, p);
+    int rc = prepare<PREC>(t, L.fwd, F, R, scr, Fm, s, mA, mA2, p, -1, nullptr, nA);
     if (rc) return rc;
     p.ldo = ldo;
     p.Fm = Fm;
     p.O = O;
     p.Y = Y;
-    return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, L.fwd, p, s);
+    return launch_tc_g<PREC, MODE_FWD>(t, mA, mA2, L.fwd, p, s, nA);
 }
 
 // Dense product (Table 3): the A operand is the caller's PDF matrix, the B
@@ -1719,11 +1792,11 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
     FK_CUDA(scr.get(&P2, (size_t)L.ntile_n * L.bwd.grp.ngroups * t->nx * R_pad));
     const TcPack *packs[2] = {&L.fwd, &L.bwd};
     float *parts[2] = {P1, P2};
-    CUtensorMap mA[2], mA2[2];
+    CUtensorMap mA[2], mA2[2], nA[2][2];
     TcParams p[2];
     PackDst pd[2];
     for (int k = 0; k < 2; ++k) {
-        const int rc = prepare<PREC>(t, *packs[k], F, R, scr, nullptr, s, mA[k], mA2[k], p[k], -1, &pd[k]);
+        const int rc = prepare<PREC>(t, *packs[k], F, R, scr, nullptr, s, mA[k], mA2[k], p[k], -1, &pd[k], nA[k]);
         if (rc) return rc;
     }
     FK_CUDA(launch_pack<PREC>(pd[0], pd[1], F, NFL * t->nxg, R, R_pad, s));
@@ -1731,7 +1804,7 @@ int bwd_tc_t(const fk_table *t, const float *F, const float *gO, int ldgo, int R
         p[k].ldo = ldgo;
         p[k].gO = gO;
         p[k].P = parts[k];
-        const int rc = launch_tc_g<PREC, MODE_ADJ>(t, mA[k], mA2[k], *packs[k], p[k], s);
+        const int rc = launch_tc_g<PREC, MODE_ADJ>(t, mA[k], mA2[k], *packs[k], p[k], s, nA[k]);
         if (rc) return rc;
     }
     k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(
@@ -1769,14 +1842,14 @@ int bwd_tc_saved_t(const fk_table *t, const float *F, const float *gO, int ldgo,
     }
     count_launch();
     FK_CUDA(cudaGetLastError());
-    CUtensorMap mA, mA2;
+    CUtensorMap mA, mA2, nA[2];
     TcParams p;
-    int rc = prepare<PREC>(t, L.bwd, F, R, scr, nullptr, s, mA, mA2, p);
+    int rc = prepare<PREC>(t, L.bwd, F, R, scr, nullptr, s, mA, mA2, p, -1, nullptr, nA);
     if (rc) return rc;
     p.ldo = ldgo;
     p.gO = gO;
     p.P = P2;
-    rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, L.bwd, p, s);
+    rc = launch_tc_g<PREC, MODE_ADJ>(t, mA, mA2, L.bwd, p, s, nA);
     if (rc) return rc;
     k_adj_gather<<<dim3((unsigned)((R + 127) / 128), (unsigned)t->nxg, NFL), 128, 0, s>>>(
         P1, P2, L.ntile_n, L.fwd.grp.ngroups, L.bwd.grp.ngroups, L.gmap, L.gmap + NFL, t->d_xinv, t->nx,
@@ -1975,6 +2048,7 @@ int tc_build(fk_table *t, const double *host_fk, unsigned form) {
         if (want_hi && (rc = make_map(&pk->half_hi, pk->hi, 2, pk->ktot_pad, rows, h))) return rc;
         if (want_lo && (rc = make_map(&pk->half_lo, pk->lo, 2, pk->ktot_pad, rows, h))) return rc;
         if (want_f32 && (rc = make_map(&pk->half_f32, pk->f32, 4, pk->ktot_pad, rows, h))) return rc;
+        if (want_lo && (rc = make_narrow_maps(*pk, rows))) return rc;
     }
     if (L.lum_on) {
         TcPack &pk = L.lum;
@@ -2074,6 +2148,7 @@ int plain_fill(fk_table *t, TcPack &pk, const double *host, int nrows, long long
     if (want_f32 && ((rc = make_map(&pk.map_f32, pk.f32, 4, pk.ktot_pad, rows, pk.n_rows)) ||
                      (rc = make_map(&pk.half_f32, pk.f32, 4, pk.ktot_pad, rows, h))))
         return rc;
+    if (want_lo && (rc = make_narrow_maps(pk, rows))) return rc;
     return FK_OK;
 }
 
@@ -2131,24 +2206,24 @@ __global__ void k_dis_scatter(const float *__restrict__ P, int R, int E, int nx,
 template <int PREC>
 int dis_tc_t(const fk_table *t, const float *F, int R, float *O, int ldo, cudaStream_t s) {
     Scratch scr(s);
-    CUtensorMap mA, mA2;
+    CUtensorMap mA, mA2, nA[2];
     TcParams p;
-    int rc = prepare<PREC>(t, t->tc.fwd, F, R, scr, nullptr, s, mA, mA2, p);
+    int rc = prepare<PREC>(t, t->tc.fwd, F, R, scr, nullptr, s, mA, mA2, p, -1, nullptr, nA);
     if (rc) return rc;
     // K (active flavours x points, at most 14 x 64) is never split: a
     // replica's result does not depend on R
     p.O = O;
     p.ldo = ldo;
-    return launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.fwd), p, s);
+    return launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.fwd), p, s, nA);
 }
 
 template <int PREC>
 int dis_bwd_tc_t(const fk_table *t, const float *gO, int ldgo, int R, float *gF, int accumulate,
                  cudaStream_t s) {
     Scratch scr(s);
-    CUtensorMap mA, mA2;
+    CUtensorMap mA, mA2, nA[2];
     TcParams p;
-    int rc = prepare<PREC>(t, t->tc.bwd, gO, R, scr, nullptr, s, mA, mA2, p, ldgo);
+    int rc = prepare<PREC>(t, t->tc.bwd, gO, R, scr, nullptr, s, mA, mA2, p, ldgo, nullptr, nA);
     if (rc) return rc;
     const int E = (int)t->E;
     float *P = nullptr;
@@ -2156,7 +2231,7 @@ int dis_bwd_tc_t(const fk_table *t, const float *gO, int ldgo, int R, float *gF,
     p.ndata = E;  // the product's rows are the table's (flavour, x) columns
     p.O = P;
     p.ldo = E;
-    rc = launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.bwd), p, s);
+    rc = launch_tc<PREC, 16, MODE_DENSE>(t, mA, mA2, b_maps<PREC>(t->tc.bwd), p, s, nA);
     if (rc) return rc;
     if (!accumulate) FK_CUDA(cudaMemsetAsync(gF, 0, sizeof(float) * (size_t)R * NFL * t->nxg, s));
     const long long n = (long long)R * E;

@@ -91,6 +91,54 @@ def test_chi2_zero_at_data_and_identity_cov():
     np.testing.assert_allclose(g[2], 2 * D, rtol=1e-14)
 
 
+@pytest.mark.parametrize("sizes,R", [([600, 10, 250], 100), ([31, 33, 64, 65], 33), ([1], 1), ([2100, 5], 3)])
+def test_chi2_fp32_io_matches_oracle(sizes, R):
+    """FP32 observables and gradient (the reduced-mode fit).  The arithmetic is
+    FP64 as for FP64 outputs, so against the oracle on the same FP32-rounded O
+    chi^2 (FP64 out) meets the 1e-12 contract of its componentwise scale and
+    gO is within its FP32 rounding plus that."""
+    cov, o = _blocks(sizes, len(sizes) + R + 11)
+    D = np.concatenate(W.pseudo_data(o, 6))
+    rng = np.random.default_rng(R + 5)
+    O32 = (np.concatenate(o)[None, :] * rng.uniform(0.9, 1.1, (R, sum(sizes)))).astype(np.float32)
+    O = O32.astype(np.float64)
+    want, B_chi = np.zeros(R), np.zeros(R)
+    g_want, B_g = np.zeros((R, sum(sizes))), np.zeros((R, sum(sizes)))
+    off = 0
+    for b in cov.blocks:
+        n = b.shape[0]
+        L = oracle.cholesky(b)
+        c, g = oracle.chi2(L, O[:, off:off + n], D[off:off + n])
+        want += c
+        g_want[:, off:off + n] = g
+        bc, bg, _, _ = solve_scales(L, O[:, off:off + n] - D[None, off:off + n])
+        B_chi += bc
+        B_g[:, off:off + n] = bg
+        off += n
+    dc = fk.Cov(cov.blocks)
+    c, g = fk.chi2(dc, torch.tensor(O32, device="cuda"), torch.tensor(D, device="cuda"))
+    torch.cuda.synchronize()
+    assert g.dtype == torch.float32
+    c, g = c.cpu().numpy(), g.double().cpu().numpy()
+    assert np.all(np.abs(c - want) <= 1e-12 * B_chi), (np.abs(c - want) / B_chi).max()
+    assert np.all(np.abs(g - g_want) <= 2.0 ** -24 * np.abs(g_want) + 1e-12 * B_g)
+    print(f"sizes {sizes}: chi2 err / scale {(np.abs(c - want) / B_chi).max():.2e}, "
+          f"gO err / |gO| {(np.abs(g - g_want) / np.maximum(np.abs(g_want), 1e-300)).max():.2e}")
+
+
+def test_chi2_fp32_io_independent_of_R():
+    sizes = [150, 40]
+    cov, o = _blocks(sizes, 9)
+    D = torch.tensor(np.concatenate(W.pseudo_data(o, 9)), device="cuda")
+    O = np.concatenate(o)[None, :] * np.random.default_rng(2).uniform(0.9, 1.1, (300, sum(sizes)))
+    Od = torch.tensor(O, dtype=torch.float32, device="cuda")
+    dc = fk.Cov(cov.blocks)
+    c, g = fk.chi2(dc, Od, D)
+    c1, g1 = fk.chi2(dc, Od[-1:].contiguous(), D)
+    assert c[-1].item() == c1[0].item()
+    assert torch.equal(g[-1], g1[0])
+
+
 def test_cov_rejects_non_spd():
     bad = np.array([[1.0, 2.0], [2.0, 1.0]])
     with pytest.raises(fk.FKError, match="positive definite"):

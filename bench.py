@@ -46,6 +46,11 @@ def save_arg(args):
     return {"auto": "auto", "on": True, "off": False}[getattr(args, "save", "auto")]
 
 
+def whiten_arg(args):
+    """GlobalFit's whiten for --whiten."""
+    return {"auto": None, "on": True, "off": False}[getattr(args, "whiten", "auto")]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -57,6 +62,9 @@ def parse():
     ap.add_argument("--save", choices=("auto", "on", "off"), default="auto",
                     help="fit case: keep the forward's tensor-core products for the adjoint (GlobalFit's "
                          "save_products: auto = where the table's ratio of table to product bytes pays)")
+    ap.add_argument("--whiten", choices=("auto", "on", "off"), default="auto",
+                    help="fit case: fold each covariance block's inverse factor into its table at set-up "
+                         "(GlobalFit's whiten: auto = every mode but the FP64 ones)")
     ap.add_argument("--inner", type=int, default=10,
                     help="fit case: fit steps per bench step (the timed region is steps x inner fit steps)")
     ap.add_argument("--no-extras", action="store_true",
@@ -1196,7 +1204,7 @@ def run_descent(args):
     t0[..., 1] = g.params.alpha[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
     t0[..., 2] = g.params.beta[None, :] * rng.uniform(0.8, 1.2, (REPLICAS, 14))
     fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
-                    save_products=save_arg(args))
+                    save_products=save_arg(args), whiten=whiten_arg(args))
     fit.capture()
     gd = PDFDescent(fit, t0, g.x, lr=0.02)
     for _ in range(max(3, args.warmup)):
@@ -1270,7 +1278,8 @@ def main():
     cov = W.covariance(o_true, SEED)
     D = np.concatenate(W.pseudo_data(o_true, SEED))
     fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
-                    pipelined=not args.phases, waves=args.waves, save_products=save_arg(args))
+                    pipelined=not args.phases, waves=args.waves, save_products=save_arg(args),
+                    whiten=whiten_arg(args))
     fit.capture()
     launches = fit.launches_per_step()
     stream = torch.cuda.current_stream()
@@ -1345,6 +1354,9 @@ def main():
             "config": dict(config_dict(g, args.prec, sum(t.device_bytes() for t in fit.tabs)), streams=fit.nstreams,
                            schedule="per-phase" if args.phases else f"pipelined, {fit.waves} forward waves",
                            fit_steps_per_step=inner, ms_per_fit_step=fit_ms,
+                           chi2=("whitened tables: L_k^-1 folded into each table and its data at set-up, "
+                                 "chi^2 = |Z - Dw|^2 per step" if fit.whiten else
+                                 "FP64 blocked substitutions per step"),
                            saved_products=f"{sum(b is not None for b in fit.saved)} of "
                                           f"{sum(k == 'had' for k in fit.kinds)} hadronic tables, "
                                           f"{sum(b.numel() * 4 for b in fit.saved if b is not None) / 1e6:.0f} MB "
@@ -1365,7 +1377,10 @@ def main():
             # only the shape is needed from here on: the 7.8 GB host copy goes
             st = W.HadTable(np.empty((st.fk.shape[0], st.fk.shape[1], st.fk.shape[2], st.fk.shape[3]),
                                      dtype=np.uint8), st.ca, st.cb, st.xmap, st.nxg)
-            line["serve"] = serve_block(args, g, fit.tabs, fit.tprec, stress_tab)
+            # the global-set tables as they are (the fit's own are whitened)
+            serve_tabs = fit.tabs if not fit.whiten else [fk.Table.from_workload(t, (args.prec,)) for t in g.tables]
+            line["serve"] = serve_block(args, g, serve_tabs, fit.tprec, stress_tab)
+            del serve_tabs
             # FP64-contract serving: FP64 results on the tensor cores, served,
             # against the plain FP64 path one request at a time (global set)
             tabs64 = [fk.Table.from_workload(t, precs=("fp64", "fp64tc")) for t in g.tables]

@@ -392,6 +392,24 @@ int fk_cov_size(const fk_cov *cov);
 int fk_chi2(const fk_cov *cov, const void *O, const double *D, int R, double *chi2, void *gO,
             int io_prec, fk_stream stream);
 
+/*
+ * chi^2 of whitened observables.  With C = L L^T, chi2 = (O - D)^T C^{-1}
+ * (O - D) = |L^{-1} O - L^{-1} D|^2, and L^{-1} O is the convolution of the
+ * tables multiplied by L^{-1} (the whitened tables, formed once when a fit is
+ * set up, since the covariance does not change during it).  Given Z = L^{-1} O
+ * and Dw = L^{-1} D:
+ *   chi2[r] = sum_i (Z[r][i] - Dw[i])^2,  gO[r][i] = 2 (Z[r][i] - Dw[i]) = d chi2[r] / d Z[r][i],
+ * which the adjoint of the whitened tables turns into d chi2 / dF.  No
+ * triangular solve is left in the step.  FP64 arithmetic; each sum runs in an
+ * order that depends on n only.  Z: DEVICE, replica r's n values at
+ * Z + r * ldz (ldz = 0: n); gO: DEVICE at gO + r * ldg (ldg = 0: n) or NULL;
+ * both double if io_prec is FK_FP64 and float otherwise.  Dw: DEVICE [n]
+ * double; chi2: DEVICE [R] double.  Asynchronous.  Errors: FK_EINVAL (NULL
+ * pointer, n < 1, R < 1, ldz or ldg < n, unknown precision), FK_ECUDA.
+ */
+int fk_chi2_white(const void *Z, int ldz, const double *Dw, int n, int R, double *chi2, void *gO, int ldg,
+                  int io_prec, fk_stream stream);
+
 /* ----------------------------------------------------- gradient descent */
 
 /*

@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import FKError, PRECS
 
 __all__ = ["Table", "conv", "dis_conv", "had_conv", "conv_backward", "saved_size", "saved_buffer", "dense_conv",
-           "luminosity", "Cov", "chi2", "FKConv", "Server", "FKError", "PRECS", "lib_path"]
+           "luminosity", "Cov", "chi2", "chi2_white", "FKConv", "Server", "FKError", "PRECS", "lib_path"]
 
 NFL = 14
 
@@ -311,6 +311,25 @@ def chi2(cov: Cov, O: torch.Tensor, D: torch.Tensor, grad=True, out=None, gO=Non
     if grad:
         g = gO if gO is not None else torch.empty_like(O)
     _lib.call("fk_chi2", cov.handle, _p(O), _p(D), R, _p(c), _p(g), io, _stream())
+    return c, g
+
+
+def chi2_white(Z: torch.Tensor, Dw: torch.Tensor, grad=True, out=None, gO=None):
+    """chi2 [R] (FP64) = |Z_r - Dw|^2 of whitened observables Z [R][n] (rows
+    of unit stride, FP64 or FP32; Dw [n] FP64 on cuda) and, if grad,
+    dchi2/dZ = 2 (Z - Dw) in Z's dtype (fk_chi2_white)."""
+    R, n = Z.shape
+    if Z.stride(1) != 1 or Dw.dtype != torch.float64 or Dw.numel() != n or not Dw.is_contiguous():
+        raise ValueError("Z must have unit column stride and Dw be a contiguous float64 [n]")
+    io = _lib.FK_FP64 if Z.dtype == torch.float64 else _lib.FK_FP32
+    c = out if out is not None else torch.empty(R, dtype=torch.float64, device=Z.device)
+    g = None
+    if grad:
+        g = gO if gO is not None else torch.empty((R, n), dtype=Z.dtype, device=Z.device)
+        if g.stride(1) != 1 or g.shape != (R, n) or g.dtype != Z.dtype:
+            raise ValueError("gO must be [R][n] with unit column stride and Z's dtype")
+    _lib.call("fk_chi2_white", _p(Z), Z.stride(0), _p(Dw), n, R, _p(c), _p(g), g.stride(0) if g is not None else 0,
+              io, _stream())
     return c, g
 
 

@@ -38,6 +38,7 @@ SIGNATURES = {
     "fk_cov_destroy": [P],
     "fk_cov_size": [P],
     "fk_chi2": [P, P, P, I, P, P, I, P],
+    "fk_chi2_white": [P, I, P, I, I, P, P, I, I, P],
     "fk_pdf_eval": [P, I, P, I, P, I, P],
     "fk_pdf_grad": [P, P, I, P, I, P, I, P],
     "fk_adam_step": [P, P, P, P, ctypes.c_longlong, I, ctypes.c_double, ctypes.c_double, ctypes.c_double,

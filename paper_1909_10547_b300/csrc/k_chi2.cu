@@ -262,6 +262,29 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_chi2_solve(CovView cv, const 
     }
 }
 
+// Whitened chi^2: with the tables and data already multiplied by L^{-1} (once,
+// when a fit is set up), Z = L^{-1} O and Dw = L^{-1} D, so z = Z - Dw,
+// chi2[r] = |z_r|^2 and d chi2 / d Z_r = 2 z_r, which the adjoint of the
+// whitened tables turns into the gradient with respect to the PDF.  FP64
+// arithmetic; one warp per replica, lane l adding i = l, l + 32, ... and a
+// butterfly sum, an order that depends on n only.  Grid ceil(R / 8), 256 threads.
+template <typename TO>
+__global__ void __launch_bounds__(256) k_chi2_white(const TO *__restrict__ Z, int ldz, const double *__restrict__ Dw,
+                                                    int n, int R, double *__restrict__ chi2, TO *__restrict__ gO,
+                                                    int ldg) {
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= R) return;  // whole warps leave together
+    const TO *z = Z + (size_t)r * ldz;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) {
+        const double d = (double)z[i] - Dw[i];
+        s = fma(d, d, s);
+        if (gO) gO[(size_t)r * ldg + i] = (TO)(2.0 * d);
+    }
+    s = warp_sum(s);
+    if (lane == 0) chi2[r] = s;
+}
+
 // chi2[r] = sum_k zsq[k][r], blocks in order.
 __global__ void k_chi2_sum(const double *__restrict__ zsq, int nblocks, int R, double *__restrict__ chi2) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,6 +462,25 @@ int fk_cov_destroy(fk_cov *cov) {
 }
 
 int fk_cov_size(const fk_cov *cov) { return cov ? cov->n : 0; }
+
+int fk_chi2_white(const void *Z, int ldz, const double *Dw, int n, int R, double *chi2, void *gO, int ldg,
+                  int io_prec, fk_stream stream) {
+    if (!Z || !Dw || !chi2) return fk::fail(FK_EINVAL, "fk_chi2_white: null pointer");
+    if (n < 1 || R < 1) return fk::fail(FK_EINVAL, "fk_chi2_white: n < 1 or R < 1");
+    if (io_prec < FK_FP64 || io_prec > FK_FP64_TC) return fk::fail(FK_EINVAL, "fk_chi2_white: unknown precision");
+    ldz = ldz ? ldz : n;
+    ldg = ldg ? ldg : n;
+    if (ldz < n || ldg < n) return fk::fail(FK_EINVAL, "fk_chi2_white: ldz or ldg < n");
+    const unsigned blocks = (unsigned)((R + 7) / 8);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (FK_IO64(io_prec))
+        fk::k_chi2_white<double><<<blocks, 256, 0, s>>>((const double *)Z, ldz, Dw, n, R, chi2, (double *)gO, ldg);
+    else
+        fk::k_chi2_white<float><<<blocks, 256, 0, s>>>((const float *)Z, ldz, Dw, n, R, chi2, (float *)gO, ldg);
+    fk::count_launch();
+    FK_CUDA(cudaGetLastError());
+    return FK_OK;
+}
 
 int fk_chi2(const fk_cov *cov, const void *O, const double *D, int R, double *chi2, void *gO,
             int io_prec, fk_stream stream) {

@@ -36,23 +36,76 @@ hi+lo) the ten largest tables of the global set gained 29-62 us per step
 from saving at rho >= 1.7, about nothing at rho = 1.1-1.4 and lost at
 rho < 1.  "auto" (default) saves where rho >= save_ratio (1.25); True
 everywhere; False nowhere.
+
+whiten (default: every mode but FP64 and FP64 on the tensor cores): the
+covariance does not change during a fit, so each block's factor is folded
+into its table and data once, at set-up (whiten_tables): with C_k = L_k L_k^T,
+the whitened table L_k^{-1} FK_k convolves to Z_k = L_k^{-1} O_k, and
+chi2_k = |Z_k - L_k^{-1} D_k|^2 with d chi2 / d Z_k = 2 (Z_k - L_k^{-1} D_k),
+which the adjoint of the whitened table turns into d chi2 / dF
+(fk_chi2_white).  The step then has no triangular solve.  The FP64 modes keep
+the substitutions of fk_chi2 and their 1e-12 contract.
 """
+import dataclasses
+
 import numpy as np
 import torch
 
-from . import Cov, Table, _lib, chi2, conv, conv_backward, grad_sum, saved_buffer
+from . import Cov, Table, _lib, chi2, chi2_white, conv, conv_backward, dense_conv, grad_sum, saved_buffer
 
 NFL = 14
 
 
+def _lower_inverse(L):
+    """L^{-1} of a lower-triangular L by forward substitution, row by row
+    (exact zeros above the diagonal)."""
+    n = L.shape[0]
+    X = np.zeros((n, n))
+    for i in range(n):
+        X[i, :i + 1] = -(L[i, :i] @ X[:i, :i + 1])
+        X[i, i] += 1.0
+        X[i, :i + 1] /= L[i, i]
+    return X
+
+
+def whiten_tables(tables, cov_blocks, D_parts, device="cuda"):
+    """(whitened tables, whitened data): per dataset k, with C_k = L_k L_k^T,
+    the table L_k^{-1} FK_k (rows of the table mixed over its data points,
+    the same channels and grid) and L_k^{-1} D_k.  The product runs on the
+    device in FP64 through the dense product (fk_dense_conv with L_k^{-1} as
+    the table and the table's transpose as the operand); L_k^{-1} and the data
+    are formed on the host (at most a few hundred rows per block)."""
+    out, Dw = [], []
+    for t, C, Dk in zip(tables, cov_blocks, D_parts):
+        n = t.ndata
+        L = np.linalg.cholesky(np.asarray(C, np.float64))
+        Li = _lower_inverse(L)
+        dtab = Table.dense(Li, precs=("fp64",))
+        E = t.fk.size // n
+        FKT = torch.tensor(np.ascontiguousarray(np.asarray(t.fk, np.float64).reshape(n, E).T), device=device)
+        Wt = dense_conv(dtab, FKT, "fp64")  # [E][n] = (L^{-1} FK)^T
+        fkw = Wt.t().contiguous().cpu().numpy().reshape(t.fk.shape)
+        dtab.close()
+        del FKT, Wt
+        out.append(dataclasses.replace(t, fk=fkw))
+        Dw.append(Li @ np.asarray(Dk, np.float64))
+    return out, Dw
+
+
 class GlobalFit:
     def __init__(self, tables, F, cov_blocks, D, prec="fp32", store=None, device="cuda",
-                 nstreams=None, pipelined=True, waves=1, save_products="auto", save_ratio=1.25):
+                 nstreams=None, pipelined=True, waves=1, save_products="auto", save_ratio=1.25, whiten=None):
         """tables: workloads.DisTable/HadTable list sharing one x grid;
         F: [R][14][nxg] replicas (host numpy); cov_blocks: one SPD block per
         table; D: [sum ndata] pseudo-data."""
         self.prec = prec
         io = torch.float64 if prec in ("fp64", "fp64tc") else torch.float32
+        self.whiten = prec not in ("fp64", "fp64tc") if whiten is None else bool(whiten)
+        if self.whiten:
+            nd0 = np.cumsum([0] + [t.ndata for t in tables])
+            D = np.asarray(D, np.float64)
+            tables, Dw = whiten_tables(tables, cov_blocks, [D[a:b] for a, b in zip(nd0, nd0[1:])], device)
+            D = np.concatenate(Dw)
         if store is None:
             store = ("fp64", "fp32") if prec in ("fp64", "fp32") else (prec,)
         self.tabs = [Table.from_workload(t, store) for t in tables]
@@ -84,8 +137,8 @@ class GlobalFit:
         if pipelined:
             # per dataset: its covariance block, and O_k, gO_k as contiguous
             # [R][n_k] blocks of one buffer
-            self.covs = [Cov([b]) for b in cov_blocks]
-            assert sum(c.n for c in self.covs) == self.ntot
+            self.covs = None if self.whiten else [Cov([b]) for b in cov_blocks]
+            assert self.whiten or sum(c.n for c in self.covs) == self.ntot
             self.Obuf = torch.empty(self.R * self.ntot, dtype=io, device=device)
             self.gObuf = torch.empty_like(self.Obuf)
             self.Ok = [self.Obuf[self.R * a:self.R * b].view(self.R, b - a) for a, b in zip(self.offs, self.offs[1:])]
@@ -93,8 +146,8 @@ class GlobalFit:
             self.Dk = [self.D[a:b] for a, b in zip(self.offs, self.offs[1:])]
             self.chi2_parts = torch.empty((len(tables), self.R), dtype=torch.float64, device=device)
         else:
-            self.cov = Cov(cov_blocks)
-            assert self.cov.n == self.ntot
+            self.cov = None if self.whiten else Cov(cov_blocks)
+            assert self.whiten or self.cov.n == self.ntot
             self.O = torch.empty((self.R, self.ntot), dtype=io, device=device)
             self.gO = torch.empty_like(self.O)
         self.graphs = None
@@ -115,7 +168,10 @@ class GlobalFit:
                 bwd += 2 * e * self.R
                 self.elems["dis"] += e
             work.append(e)
-        self.flops = {"forward": fwd, "loss": 2 * int(sum(n * n for n in nd)) * self.R, "backward": bwd}
+        # the loss: both substitutions (n_k^2 multiply-adds per replica), or for
+        # whitened tables one subtraction and one multiply-add per data point
+        loss = 2 * self.ntot * self.R if self.whiten else 2 * int(sum(n * n for n in nd)) * self.R
+        self.flops = {"forward": fwd, "loss": loss, "backward": bwd}
         # streams: greedy assignment of tables (largest first) to the least
         # loaded stream; by default one stream per table (up to the 64
         # gradient parts that grad_sum combines), so that the small per-table
@@ -151,7 +207,7 @@ class GlobalFit:
         # (1.24 -> 1.19 ms measured; priority -2, above the light streams,
         # measured 1.22)
         self.chi2_streams = ([torch.cuda.Stream(device=device, priority=-1) for _ in tables]
-                             if pipelined else [])
+                             if pipelined and not self.whiten else [])
 
     # -- helpers -------------------------------------------------------------
     def _fan_out(self, body):
@@ -180,7 +236,10 @@ class GlobalFit:
         self._fan_out(body)
 
     def loss(self):
-        chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)
+        if self.whiten:
+            chi2_white(self.O, self.D, out=self.chi2, gO=self.gO)
+        else:
+            chi2(self.cov, self.O, self.D, grad=True, out=self.chi2, gO=self.gO)
 
     def backward(self):
         def body(s):
@@ -238,13 +297,17 @@ class GlobalFit:
         conv(self.tabs[k], self.F, self.tprec[k], out=self.Ok[k], save=self.saved[k])
         fwd = torch.cuda.Event()
         fwd.record(cur)
-        h = self.chi2_streams[k]
-        h.wait_event(fwd)
-        with torch.cuda.stream(h):
-            chi2(self.covs[k], self.Ok[k], self.Dk[k], grad=True, out=self.chi2_parts[k], gO=self.gOk[k])
-            done = torch.cuda.Event()
-            done.record(h)
-        cur.wait_event(done)
+        if self.whiten:
+            # one short kernel: on the chain's own stream
+            chi2_white(self.Ok[k], self.Dk[k], out=self.chi2_parts[k], gO=self.gOk[k])
+        else:
+            h = self.chi2_streams[k]
+            h.wait_event(fwd)
+            with torch.cuda.stream(h):
+                chi2(self.covs[k], self.Ok[k], self.Dk[k], grad=True, out=self.chi2_parts[k], gO=self.gOk[k])
+                done = torch.cuda.Event()
+                done.record(h)
+            cur.wait_event(done)
         conv_backward(self.tabs[k], self.F, self.gOk[k], self.tprec[k], gF=self.gF_parts[s],
                       accumulate=accumulate, saved=self.saved[k])
         return fwd

@@ -148,3 +148,13 @@ def test_saved_product_argument_errors_need_no_gpu():
     assert lib.fk_had_conv_save(None, p, 1, p, 0, p, 1 << 20, _lib.FK_BF16X3, None) == _lib.FK_EINVAL
     assert lib.fk_conv_backward_saved(None, p, p, 0, 1, p, 1 << 20, p, 0, _lib.FK_BF16X3,
                                       None) == _lib.FK_EINVAL
+
+
+def test_chi2_white_argument_errors_need_no_gpu():
+    lib = _lib.load()
+    p = ctypes.c_void_p(16)
+    assert lib.fk_chi2_white(None, 0, p, 4, 2, p, None, 0, _lib.FK_FP64, None) == _lib.FK_EINVAL  # no Z
+    assert lib.fk_chi2_white(p, 0, p, 0, 2, p, None, 0, _lib.FK_FP64, None) == _lib.FK_EINVAL     # n < 1
+    assert lib.fk_chi2_white(p, 3, p, 4, 2, p, None, 0, _lib.FK_FP64, None) == _lib.FK_EINVAL     # ldz < n
+    assert lib.fk_chi2_white(p, 0, p, 4, 2, p, p, 2, _lib.FK_FP64, None) == _lib.FK_EINVAL        # ldg < n
+    assert lib.fk_chi2_white(p, 0, p, 4, 2, p, None, 0, 99, None) == _lib.FK_EINVAL               # precision

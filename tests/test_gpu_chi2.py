@@ -139,6 +139,58 @@ def test_chi2_fp32_io_independent_of_R():
     assert torch.equal(g[-1], g1[0])
 
 
+@pytest.mark.parametrize("sizes,R,dtype", [([600, 10, 250], 100, torch.float64), ([31, 33], 7, torch.float32),
+                                           ([1], 1, torch.float64)])
+def test_chi2_white_matches_oracle(sizes, R, dtype):
+    """chi^2 of whitened observables: with Z = L^{-1} O and Dw = L^{-1} D
+    (formed here in FP64 on the host), |Z - Dw|^2 is the oracle's
+    (O - D)^T C^{-1} (O - D) within 1e-12 of its scale, and d chi2/dZ = 2 z is
+    L^T times the oracle's d chi2/dO (2 L^-T z)."""
+    cov, o = _blocks(sizes, len(sizes) + R + 3)
+    D = np.concatenate(W.pseudo_data(o, 7))
+    rng = np.random.default_rng(R + 9)
+    O = np.concatenate(o)[None, :] * rng.uniform(0.9, 1.1, (R, sum(sizes)))
+    if dtype == torch.float32:
+        O = O.astype(np.float32).astype(np.float64)
+    Z, Dw, want, B_chi = np.zeros_like(O), np.zeros_like(D), np.zeros(R), np.zeros(R)
+    gz_want = np.zeros_like(O)
+    off = 0
+    for b in cov.blocks:
+        n = b.shape[0]
+        L = oracle.cholesky(b)
+        c, g = oracle.chi2(L, O[:, off:off + n], D[off:off + n])
+        want += c
+        Z[:, off:off + n] = np.linalg.solve(L, O[:, off:off + n].T).T
+        Dw[off:off + n] = np.linalg.solve(L, D[off:off + n])
+        gz_want[:, off:off + n] = g @ L  # dchi2/dZ = L^T dchi2/dO, row form
+        bc, _, _, _ = solve_scales(L, O[:, off:off + n] - D[None, off:off + n])
+        B_chi += bc
+        off += n
+    Zd = torch.tensor(Z, dtype=dtype, device="cuda")
+    c, gz = fk.chi2_white(Zd, torch.tensor(Dw, device="cuda"))
+    torch.cuda.synchronize()
+    c, gz = c.cpu().numpy(), gz.double().cpu().numpy()
+    if dtype == torch.float32:  # Z itself rounded to FP32: compare with its own exact sum
+        Zr = Zd.double().cpu().numpy()
+        want = ((Zr - Dw) ** 2).sum(axis=1)
+        np.testing.assert_allclose(c, want, rtol=1e-13)
+        np.testing.assert_allclose(gz, (2 * (Zr - Dw)).astype(np.float32), rtol=0, atol=0)
+        return
+    assert np.all(np.abs(c - want) <= 1e-12 * B_chi), (np.abs(c - want) / B_chi).max()
+    assert np.abs(gz - gz_want).max() <= 1e-12 * np.abs(gz_want).max()
+
+
+def test_chi2_white_strides_and_errors():
+    Z = torch.tensor(np.random.default_rng(3).standard_normal((5, 12)), device="cuda")
+    Dw = torch.tensor(np.random.default_rng(4).standard_normal(7), device="cuda")
+    c, g = fk.chi2_white(Z[:, 2:9], Dw)
+    ref = ((Z[:, 2:9].cpu().numpy() - Dw.cpu().numpy()) ** 2).sum(axis=1)
+    np.testing.assert_allclose(c.cpu().numpy(), ref, rtol=1e-14)
+    assert torch.equal(g, 2 * (Z[:, 2:9] - Dw))
+    with pytest.raises(ValueError):
+        fk.chi2_white(Z, Dw)  # Dw of the wrong length
+
+
 def test_cov_rejects_non_spd():
     bad = np.array([[1.0, 2.0], [2.0, 1.0]])
     with pytest.raises(fk.FKError, match="positive definite"):

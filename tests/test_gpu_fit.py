@@ -193,3 +193,52 @@ def test_saved_products_do_not_change_the_step(small_global, pipelined):
     for chi, gF in res[1:]:
         assert np.array_equal(chi, res[0][0])
         assert np.array_equal(gF, res[0][1])
+
+
+def test_whitened_tables(small_global):
+    """whiten_tables (the dense FP64 product on the device) gives L^{-1} FK and
+    L^{-1} D of each dataset as forward substitution with the same factor L
+    does (a componentwise-accurate solve: a pivoting LU solve is not, its row 0
+    picks up the rounding of the larger rows).  Both carry errors of order
+    kappa(L) u64 of the componentwise scale |L^{-1}| |FK|; they agree to 1e-10
+    of it, where a wrong index or transpose would be off by O(1).  (Another
+    factorisation of C differs from L by kappa(C) u64, which L^{-1} can amplify
+    past that bound, so the reference uses numpy's, as whiten_tables does.)"""
+    from scipy.linalg import solve_triangular
+
+    from paper_1909_10547_b300.fitstep import whiten_tables
+    g, cov, D = small_global
+    wt, Dw = whiten_tables(g.tables, cov.blocks, D)
+    for t, w, b, d, dw in zip(g.tables, wt, cov.blocks, D, Dw):
+        L = np.linalg.cholesky(b)
+        n = t.ndata
+        ref = solve_triangular(L, t.fk.reshape(n, -1), lower=True).reshape(t.fk.shape)
+        aLi = np.abs(solve_triangular(L, np.eye(n), lower=True))
+        scale = aLi @ np.abs(t.fk.reshape(n, -1))
+        assert np.all(np.abs(w.fk - ref).reshape(n, -1) <= 1e-10 * scale)
+        assert np.all(np.abs(dw - solve_triangular(L, d, lower=True)) <= 1e-10 * (aLi @ np.abs(d)))
+        assert type(w) is type(t) and w.fk.shape == t.fk.shape
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16x3", 1e-4)])
+def test_whitened_step_matches_plain(small_global, prec, tol):
+    """The step on whitened tables (the default in the non-FP64 modes) gives
+    the chi^2 and gradient of the step with the substitutions: the same
+    quantities, rounded differently (relative to the oracle's scales)."""
+    g, cov, D = small_global
+    res = []
+    for whiten in (False, True):
+        fit = GlobalFit(g.tables, g.F, cov.blocks, np.concatenate(D), prec=prec, whiten=whiten)
+        assert fit.whiten == whiten
+        fit.step()
+        torch.cuda.synchronize()
+        res.append((fit.chi2.cpu().numpy().copy(), fit.gF.double().cpu().numpy().copy()))
+    chi_ref, gF_ref = oracle_chain(g, cov, D, g.F)
+    (c0, g0), (c1, g1) = res
+    for c, gg in res:
+        assert np.abs(c - chi_ref).max() <= tol * np.abs(chi_ref).max()
+        assert np.abs(gg - gF_ref).max() <= 2 * tol * np.abs(gF_ref).max()
+    print(prec, "chi2 rel err plain", (np.abs(c0 - chi_ref) / np.abs(chi_ref)).max(),
+          "whitened", (np.abs(c1 - chi_ref) / np.abs(chi_ref)).max(),
+          "grad rel err plain", np.abs(g0 - gF_ref).max() / np.abs(gF_ref).max(),
+          "whitened", np.abs(g1 - gF_ref).max() / np.abs(gF_ref).max())

@@ -423,6 +423,28 @@ def roof_entry(prec, byts, flops, ms, kernel, traffic=None):
     return r
 
 
+def chi2_line(args, cov, o_true, D, R=REPLICAS):
+    """The FP64 chi^2 with its gradient (blocked forward and back
+    substitutions, fk_chi2) on the global set's 40 covariance blocks, R = 100
+    replicas of FP32 observables: the fit step itself runs on whitened tables,
+    so the solve is timed here.  Roofline: the FP64 pipe, sum n_k^2 R
+    multiply-adds (both substitutions)."""
+    import torch
+    import paper_1909_10547_b300 as fk
+    dcov = fk.Cov(cov.blocks)
+    o = np.concatenate(o_true)
+    rng = np.random.default_rng(SEED + 2)
+    O = torch.tensor(o[None, :] * rng.uniform(0.9, 1.1, (R, o.size)), dtype=torch.float32, device="cuda")
+    Dd = torch.tensor(np.asarray(D, np.float64), device="cuda")
+    c = torch.empty(R, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(O)
+    ms = time_calls(lambda: fk.chi2(dcov, O, Dd, out=c, gO=g), max(args.steps, 20))
+    nn = int(sum(b.shape[0] ** 2 for b in cov.blocks))
+    return {"name": f"FP64 chi^2 + gradient, blocked substitutions, {len(cov.blocks)} blocks ({o.size} points), "
+                    f"R={R}", "prec": "fp64", "value": o.size * R / (ms * 1e-3), "unit": UNIT, "ms": ms,
+            "roofline": roof_entry("fp64", 2 * nn * 8, 2.0 * nn * R, ms, "k_chi2_solve (one launch per call)")}
+
+
 def kernel_lines(args, stress_tab=None, stress_t=None, stress_oz=None):
     """Kernel-level lines: each one call of one path, timed on its own with
     its own roofline.  Stress table (2000 x 196 channels x 50 x 50; resident
@@ -1388,6 +1410,7 @@ def main():
                                              plain_prec="fp64")
             del tabs64
             line["kernels"] = kernel_lines(args, stress_tab, st, stress_oz)
+            line["kernels"].append(chi2_line(args, cov, o_true, D))
             del st, stress_oz, stress_tab
             torch.cuda.synchronize()
         except Exception as exc:  # the headline stands; say what failed

@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(tc_threads<MODE>(), 1)
                         }
                     }
                 }
-                if (MODE == MODE_ADJ) {
+                if (MODE == MODE_ADJ && r < p.R) {  // padding replicas: never gathered
                     float *pg = p.P + (((size_t)nt * p.ngroups + g) * p.nx) * p.R_pad + r;
                     if (FK_DBG(nt < p.ntile_n && r < p.R_pad, 14, nt)) {
 #pragma unroll
@@ -1183,8 +1183,8 @@ __global__ void k_pack_lum(const double *__restrict__ fk, int ndata, int nc, int
 // the order in which the adjoint epilogue forms it from the accumulator, so
 // P1 is the one the tensor-core pass over the forward packing would write.
 // The forward stores no products for padding replicas (r >= R): their
-// threads read replica R - 1's (written, finite) with weights 0, so their
-// partial sums are 0 as in that pass.
+// threads read replica R - 1's (written, finite) with weights 0 and write
+// nothing (the gather reads replicas below R only).
 // Grid (R_pad / 128 * ADJ_XS, ngroups, ntile): replicas across threads
 // (coalesced loads of Y and stores of P1), the x points split over ADJ_XS
 // blocks, the tile's G weights in registers, the loads of UI x points in
@@ -1223,7 +1223,7 @@ __global__ void __launch_bounds__(128) k_adj_saved(const float *__restrict__ Y, 
             float ps = 0.f;
 #pragma unroll
             for (int dl = 0; dl < G; ++dl) ps = fmaf(w[dl], v[u][dl], ps);
-            if (i0 + u < iend) o[(size_t)(i0 + u) * R_pad] = ps;
+            if (i0 + u < iend && r < R) o[(size_t)(i0 + u) * R_pad] = ps;
         }
     }
 }

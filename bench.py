@@ -22,6 +22,7 @@ streaming and R = 1000 tensor cores, configs 0-2, Table 3's R = 1 rows) and
 at 2000/s, p50/p99/max latency, saturation and per-request throughput).
 """
 import argparse
+import faulthandler
 import hashlib
 import json
 import os
@@ -39,6 +40,14 @@ METRIC = "FK conv datapoint·replicas/s"
 UNIT = "datapoint·replicas/s"
 REPLICAS = 100
 SEED = 10547 + 3
+
+
+_T0 = time.perf_counter()
+
+
+def stage(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def save_arg(args):
@@ -65,6 +74,9 @@ def parse():
     ap.add_argument("--whiten", choices=("auto", "on", "off"), default="auto",
                     help="fit case: fold each covariance block's inverse factor into its table at set-up "
                          "(GlobalFit's whiten: auto = every mode but the FP64 ones)")
+    ap.add_argument("--watchdog-s", type=float, default=900.0,
+                    help="print every thread's stack to stderr and exit if the run has not finished after this "
+                         "many seconds (the default run takes a few minutes); 0 disables")
     ap.add_argument("--inner", type=int, default=10,
                     help="fit case: fit steps per bench step (the timed region is steps x inner fit steps)")
     ap.add_argument("--no-extras", action="store_true",
@@ -615,20 +627,27 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0, plai
     # warm-up: every (table, R) pair of the run once through the server and
     # once through the plain path, so that no kernel is loaded (the CUDA
     # runtime loads each kernel on its first launch) inside the timed runs
+    stage(f"  serve: warm-up of {len(alltabs)} tables")
     seen = {}
     for w, F, p in work:
         seen.setdefault((w, F.shape[0]), (w, F, p))
     for w, F, p in seen.values():
-        srv.wait(srv.submit(ids[w], F, p), 600000)
+        srv.wait(srv.submit(ids[w], F, p), 120000)
         fk.conv(alltabs[w], torch.from_numpy(F).to("cuda"), plain_prec or p).cpu()
     tickets = [None] * n
     t_sub = np.zeros(n)
     t_done = np.zeros(n)
 
+    poll_err = []
+
     def poller():
         outstanding = set()
         nxt = 0
+        deadline = time.perf_counter() + 300.0
         while nxt < n or outstanding:
+            if time.perf_counter() > deadline:
+                poll_err.append(f"{len(outstanding)} requests unresolved after 300 s")
+                return
             while nxt < n and tickets[nxt] is not None:
                 outstanding.add(nxt)
                 nxt += 1
@@ -639,7 +658,8 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0, plai
                     outstanding.discard(k)
             time.sleep(0.0001)
 
-    th = threading.Thread(target=poller)
+    th = threading.Thread(target=poller, daemon=True)
+    stage(f"  serve: open loop, {n} requests")
     th.start()
     t0 = time.perf_counter()
     for k, (w, F, p) in enumerate(work):
@@ -649,16 +669,18 @@ def serve_block(args, g, tabs, tprec, stress_tab=None, n=2000, rate=2000.0, plai
         t_sub[k] = time.perf_counter()
         tickets[k] = srv.submit(ids[w], F, p)
     th.join()
+    if poll_err:
+        raise TimeoutError("served mix: " + poll_err[0])
     lat = (t_done - t_sub) * 1e3
     span = t_done.max() - t_sub.min()
     s0 = time.perf_counter()
     inflight = []
     for w, F, p in work:
         if len(inflight) >= 64:
-            srv.wait(inflight.pop(0), 600000)
+            srv.wait(inflight.pop(0), 120000)
         inflight.append(srv.submit(ids[w], F, p))
     for tk in inflight:
-        srv.wait(tk, 600000)
+        srv.wait(tk, 120000)
     sat = time.perf_counter() - s0
     st = srv.stats()
     srv.close()
@@ -1131,7 +1153,10 @@ def run_serve(args):
     def poller():
         outstanding = set()
         nxt = 0
+        deadline = time.perf_counter() + 300.0
         while nxt < n or outstanding:
+            if time.perf_counter() > deadline:
+                return  # done_flag stays False: reported below
             while nxt < n and tickets[nxt] is not None:
                 outstanding.add(nxt)
                 nxt += 1
@@ -1143,7 +1168,7 @@ def run_serve(args):
             time.sleep(0.0001)
         done_flag[0] = True
 
-    th = threading.Thread(target=poller)
+    th = threading.Thread(target=poller, daemon=True)
     th.start()
     t0 = time.perf_counter()
     for k, (w, F, p) in enumerate(work):
@@ -1153,6 +1178,8 @@ def run_serve(args):
         t_sub[k] = time.perf_counter()
         tickets[k] = srv.submit(ids[w], F, p)
     th.join()
+    if not done_flag[0]:
+        raise TimeoutError("served mix: requests unresolved after 300 s")
     lat = (t_done - t_sub) * 1e3
     span = t_done.max() - t_sub.min()
     st = srv.stats()
@@ -1163,10 +1190,10 @@ def run_serve(args):
     inflight = []
     for w, F, p in work:
         if len(inflight) >= WINDOW:
-            srv.wait(inflight.pop(0), 600000)
+            srv.wait(inflight.pop(0), 120000)
         inflight.append(srv.submit(ids[w], F, p))
     for tk in inflight:
-        srv.wait(tk, 600000)
+        srv.wait(tk, 120000)
     sat_span = time.perf_counter() - s0
     srv.close()
 
@@ -1261,6 +1288,8 @@ def run_descent(args):
 
 def main():
     args = parse()
+    if args.watchdog_s > 0:
+        faulthandler.dump_traceback_later(args.watchdog_s, exit=True)
     import torch
     if args.case == "stress":
         run_stress(args)
@@ -1302,6 +1331,7 @@ def main():
     fit = GlobalFit(g.tables, g.F, cov.blocks, D, prec=args.prec, nstreams=args.streams or None,
                     pipelined=not args.phases, waves=args.waves, save_products=save_arg(args),
                     whiten=whiten_arg(args))
+    stage("fit step set up (tables, whitening, saved-product buffers)")
     fit.capture()
     launches = fit.launches_per_step()
     stream = torch.cuda.current_stream()
@@ -1360,6 +1390,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps)
+    stage("fit step timed (device and end to end)")
 
     units = fit.ntot * fit.R * inner
     value = job_throughput(units, world, ms)
@@ -1401,14 +1432,17 @@ def main():
                                      dtype=np.uint8), st.ca, st.cb, st.xmap, st.nxg)
             # the global-set tables as they are (the fit's own are whitened)
             serve_tabs = fit.tabs if not fit.whiten else [fk.Table.from_workload(t, (args.prec,)) for t in g.tables]
+            stage("serving block")
             line["serve"] = serve_block(args, g, serve_tabs, fit.tprec, stress_tab)
             del serve_tabs
             # FP64-contract serving: FP64 results on the tensor cores, served,
             # against the plain FP64 path one request at a time (global set)
             tabs64 = [fk.Table.from_workload(t, precs=("fp64", "fp64tc")) for t in g.tables]
+            stage("FP64-contract serving block")
             line["serve_fp64"] = serve_block(args, g, tabs64, ["fp64tc"] * len(tabs64), None, n=400,
                                              plain_prec="fp64")
             del tabs64
+            stage("kernel lines")
             line["kernels"] = kernel_lines(args, stress_tab, st, stress_oz)
             line["kernels"].append(chi2_line(args, cov, o_true, D))
             del st, stress_oz, stress_tab
@@ -1417,6 +1451,7 @@ def main():
             line["extras_error"] = f"{type(exc).__name__}: {exc}"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         D_parts = np.split(D, np.cumsum([t.ndata for t in g.tables])[:-1])
+        stage("CPU baseline (oracle)")
         cb = cpu_baseline(g, cov.blocks, D_parts)
         nr = cb["replicas"]
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",

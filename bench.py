@@ -5,7 +5,11 @@
 A fit step is one pass of the whole hot path over the global-shaped fit set
 (40 synthetic datasets, 12 DIS + 28 hadronic, ~4500 data points, R = 100
 replicas on a shared 50-point x grid): forward convolution of every table,
-FP64 chi^2 with its gradient, adjoint of every table into dchi2/dF.  A bench
+chi^2 with its gradient, adjoint of every table into dchi2/dF.  In the
+non-FP64 modes the tables and data are whitened once at set-up (each
+covariance block's inverse Cholesky factor folded in, --whiten), so the
+step's chi^2 needs no triangular solve; the FP64 modes (and --whiten off)
+run the FP64 substitutions in the step.  A bench
 step is --inner (default 10) consecutive fit steps, so that the timed region
 of the driver's step count lasts a quarter of a second or more.  The metric
 is datapoint*replicas per second (sum of ndata * R over the fit steps,
@@ -17,7 +21,8 @@ prints one JSON line.
 With one GPU the line also carries: `accuracy` (the fit step's chi^2 and
 gradient against the FP64 oracle, from the CPU-baseline leg's own run),
 `kernels` (kernel-level lines with their own rooflines: stress table R = 1
-streaming and R = 1000 tensor cores, configs 0-2, Table 3's R = 1 rows) and
+streaming and R = 1000 tensor cores, configs 0-2, Table 3's R = 1 rows, the
+FP64 chi^2 substitutions alone) and
 `serve` (a bounded run of the served mixed workload: 2000 Poisson arrivals
 at 2000/s, p50/p99/max latency, saturation and per-request throughput).
 """

@@ -12,12 +12,13 @@ The covariance is block diagonal with one block per dataset, so the three
 stages of dataset k depend only on each other.  All run in libfk.so kernels.
 
 pipelined=True (default): each table's chain forward -> chi^2 block ->
-adjoint runs on its own CUDA stream (the chi^2 forked onto a high-priority
-stream of its own and joined back), so the FP64 chi^2 of one dataset
-overlaps the tensor-core and CUDA-core convolutions of the others; the
-per-stream gradient buffers and the per-dataset chi^2 values are then added
-by fk_grad_sum in a fixed order.  capture() records the step as one CUDA
-graph whose streams are parallel branches.
+adjoint runs on its own CUDA stream, so the work of one dataset overlaps the
+convolutions of the others (with the FP64 substitutions, the chi^2 is forked
+onto a high-priority stream of its own and joined back; on whitened tables
+it is one short kernel on the chain's stream); the per-stream gradient
+buffers and the per-dataset chi^2 values are then added by fk_grad_sum in a
+fixed order.  capture() records the step as one CUDA graph whose streams are
+parallel branches.
 
 pipelined=False: three phases (all forwards, one chi^2 launch over all
 blocks, all adjoints), each its own graph, for per-phase timing.
